@@ -1,0 +1,724 @@
+"""Pins of the FP64 oracle against things other than itself: values the paper
+prints, closed forms, invariants, brute force and finite differences.
+
+Each pin is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign or index, a transposed operand) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2310_17274_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# helpers (independent of the oracle's code)
+# ---------------------------------------------------------------------------
+
+def _mat4(tf12):
+    T = np.eye(4)
+    T[:3, :] = np.asarray(tf12).reshape(3, 4)
+    return T
+
+
+def _robot(spheres=synth.SPHERES_42, seed=0):
+    return synth.make_robot(spheres, seed=seed)
+
+
+def _chain(n_joints, axes=None, spheres_per_link=2, seed=5):
+    """A short chain for finite-difference pins."""
+    axes = axes or [2, 1, 0, 2, 1, 0, 2][:n_joints]
+    rb = synth.make_robot(tuple([spheres_per_link] * n_joints), seed=seed, axes=tuple(axes))
+    return rb
+
+
+def _quat_axis_angle(axis, ang):
+    axis = np.asarray(axis, dtype=float) / np.linalg.norm(axis)
+    return np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * axis])
+
+
+# ---------------------------------------------------------------------------
+# constants the paper states
+# ---------------------------------------------------------------------------
+
+def test_default_constants_match_paper(oracle_mod):
+    p = oracle_mod.params_default()
+    with open(os.path.join(GOLDEN, "paper_constants.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            name, value = line.split()[:2]
+            if name == "alpha":
+                assert p["alpha"] == [float(v) for v in value.split(",")]
+            else:
+                assert p[name] == pytest.approx(float(value), rel=0, abs=0), name
+
+
+# ---------------------------------------------------------------------------
+# forward kinematics (Sec. 3.1, App. E.1 Table "Joint Transformation matrices")
+# ---------------------------------------------------------------------------
+
+def test_joint_axes_match_table(oracle_mod):
+    """One joint with F = I at theta = pi/2 moves unit points as the table's
+    revolute matrices do."""
+    with open(os.path.join(GOLDEN, "joint_transform_axes.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for ax, *vals in rows:
+        a = "xyz".index(ax)
+        inp = np.array(vals[:3], dtype=float)
+        exp = np.array(vals[3:], dtype=float)
+        ident = np.eye(3, 4).reshape(12)
+        rb = synth.Robot(fixed_tf=np.stack([ident, ident]), axis=np.array([a], np.int32),
+                         q_lo=np.array([-3.0]), q_hi=np.array([3.0]), v_max=np.ones(1),
+                         a_max=np.ones(1), j_max=np.ones(1),
+                         spheres=np.array([[*inp, 0.1]]), sphere_link=np.array([0], np.int32),
+                         pairs=np.zeros((0, 2), np.int32))
+        _, sp, _ = oracle_mod.fk(rb, [math.pi / 2])
+        np.testing.assert_allclose(sp[0, :3], exp, atol=1e-15)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_full_link_transformation_matches_table(oracle_mod, axis):
+    """Right-hand column of the table: F * J(theta) written entrywise with
+    f_0..f_11 (the X row's (3,3) entry read as f_10 cos, the printed
+    "f_10 sin" being a typo)."""
+    rng = np.random.default_rng(axis)
+    f = rng.normal(size=12)
+    th = 0.7
+    c, s = math.cos(th), math.sin(th)
+    if axis == 0:
+        exp = [f[0], f[1] * c + f[2] * s, -f[1] * s + f[2] * c, f[3],
+               f[4], f[5] * c + f[6] * s, -f[5] * s + f[6] * c, f[7],
+               f[8], f[9] * c + f[10] * s, -f[9] * s + f[10] * c, f[11]]
+    elif axis == 1:
+        exp = [f[0] * c - f[2] * s, f[1], f[0] * s + f[2] * c, f[3],
+               f[4] * c - f[6] * s, f[5], f[4] * s + f[6] * c, f[7],
+               f[8] * c - f[10] * s, f[9], f[8] * s + f[10] * c, f[11]]
+    else:
+        exp = [f[0] * c + f[1] * s, -f[0] * s + f[1] * c, f[2], f[3],
+               f[4] * c + f[5] * s, -f[4] * s + f[5] * c, f[6], f[7],
+               f[8] * c + f[9] * s, -f[8] * s + f[9] * c, f[10], f[11]]
+    ident = np.eye(3, 4).reshape(12)
+    rb = synth.Robot(fixed_tf=np.stack([f, ident]), axis=np.array([axis], np.int32),
+                     q_lo=np.array([-3.0]), q_hi=np.array([3.0]), v_max=np.ones(1),
+                     a_max=np.ones(1), j_max=np.ones(1), spheres=np.zeros((0, 4)),
+                     sphere_link=np.zeros(0, np.int32), pairs=np.zeros((0, 2), np.int32))
+    lt, _, _ = oracle_mod.fk(rb, [th])
+    np.testing.assert_allclose(lt[0], exp, atol=1e-14)
+
+
+def test_fk_zero_configuration_is_composed_fixed_transforms(oracle_mod):
+    rb = _robot()
+    lt, sp, ee = oracle_mod.fk(rb, np.zeros(rb.dof))
+    T = np.eye(4)
+    for j in range(rb.dof):
+        T = T @ _mat4(rb.fixed_tf[j])
+        np.testing.assert_allclose(lt[j], T[:3].reshape(12), atol=1e-14)
+    np.testing.assert_allclose(ee, (T @ _mat4(rb.fixed_tf[rb.dof]))[:3].reshape(12), atol=1e-14)
+    for i in range(rb.n_spheres):
+        Tl = np.eye(4)
+        for j in range(rb.sphere_link[i] + 1):
+            Tl = Tl @ _mat4(rb.fixed_tf[j])
+        np.testing.assert_allclose(sp[i, :3], (Tl @ np.r_[rb.spheres[i, :3], 1])[:3], atol=1e-14)
+        assert sp[i, 3] == rb.spheres[i, 3]
+
+
+def test_fk_rigidity_and_orthonormality(oracle_mod):
+    rb = _robot()
+    rng = np.random.default_rng(1)
+    _, sp0, _ = oracle_mod.fk(rb, np.zeros(rb.dof))
+    for _ in range(5):
+        q = synth.uniform_config(rng, rb)
+        lt, sp, ee = oracle_mod.fk(rb, q)
+        for T in list(lt) + [ee]:
+            R = np.asarray(T).reshape(3, 4)[:, :3]
+            assert np.abs(R.T @ R - np.eye(3)).max() < 1e-12
+            assert abs(np.linalg.det(R) - 1) < 1e-12
+        for l in range(rb.dof):
+            idx = np.where(rb.sphere_link == l)[0]
+            d0 = np.linalg.norm(sp0[idx, None, :3] - sp0[None, idx, :3], axis=-1)
+            d1 = np.linalg.norm(sp[idx, None, :3] - sp[None, idx, :3], axis=-1)
+            np.testing.assert_allclose(d0, d1, atol=1e-12)
+
+
+def test_fk_first_joint_rotation_is_rigid_about_base_axis(oracle_mod):
+    """Turning joint 0 (a z joint at the base) by phi rotates every sphere
+    about the world z axis by phi."""
+    rb = _robot()
+    rng = np.random.default_rng(3)
+    q = synth.uniform_config(rng, rb) * 0.5
+    _, sp, _ = oracle_mod.fk(rb, q)
+    q2 = q.copy()
+    q2[0] += 0.4
+    _, sp2, _ = oracle_mod.fk(rb, q2)
+    c, s = math.cos(0.4), math.sin(0.4)
+    Rz = np.array([[c, -s, 0], [s, c, 0], [0, 0, 1]])
+    np.testing.assert_allclose(sp2[:, :3], sp[:, :3] @ Rz.T, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# box signed distance (Sec. 3.5)
+# ---------------------------------------------------------------------------
+
+def _box(seed=0):
+    rng = np.random.default_rng(seed)
+    pose = np.concatenate([rng.uniform(-0.5, 0.5, 3),
+                           _quat_axis_angle(rng.normal(size=3), rng.uniform(0, 3))])
+    he = rng.uniform(0.05, 0.3, 3)
+    return pose, he
+
+
+def _rot(q):
+    w, x, y, z = q / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def test_sphere_at_box_centre(oracle_mod):
+    """Sphere-in-box distance at the centre = -(min half-extent gap + radius)."""
+    for seed in range(4):
+        pose, he = _box(seed)
+        phi, _ = oracle_mod.box_sdf(pose, he, pose[:3])
+        r = 0.05
+        assert phi - r == pytest.approx(-(he.min() + r), abs=1e-14)
+
+
+def test_box_face_and_corner_regions(oracle_mod):
+    pose, he = _box(7)
+    R = _rot(pose[3:])
+    # face region along local +y
+    u = np.array([0.3 * he[0], he[1] + 0.17, -0.2 * he[2]])
+    phi, g = oracle_mod.box_sdf(pose, he, pose[:3] + R @ u)
+    assert phi == pytest.approx(0.17, abs=1e-12)
+    np.testing.assert_allclose(g, R[:, 1], atol=1e-12)
+    # corner region
+    u = he * np.array([1, -1, 1]) + np.array([0.1, -0.2, 0.05])
+    phi, g = oracle_mod.box_sdf(pose, he, pose[:3] + R @ u)
+    assert phi == pytest.approx(math.sqrt(0.1 ** 2 + 0.2 ** 2 + 0.05 ** 2), abs=1e-12)
+    # inside, closest to local -x face
+    u = np.array([-he[0] + 0.01, 0.0, 0.0])
+    if he[0] - 0.01 < min(he[1], he[2]):
+        phi, g = oracle_mod.box_sdf(pose, he, pose[:3] + R @ u)
+        assert phi == pytest.approx(-0.01, abs=1e-12)
+        np.testing.assert_allclose(g, -R[:, 0], atol=1e-12)
+
+
+def test_box_sdf_brute_force(oracle_mod):
+    """Distance to a densely sampled box surface (minus inside)."""
+    pose, he = _box(3)
+    R = _rot(pose[3:])
+    n = 60
+    grids = []
+    lin = [np.linspace(-h, h, n) for h in he]
+    for a in range(3):
+        for sgn in (-1, 1):
+            b, c = [k for k in range(3) if k != a]
+            B, Cc = np.meshgrid(lin[b], lin[c], indexing="ij")
+            P = np.zeros((n * n, 3))
+            P[:, a] = sgn * he[a]
+            P[:, b] = B.ravel()
+            P[:, c] = Cc.ravel()
+            grids.append(P)
+    surf = np.concatenate(grids)
+    step = 2 * he.max() / (n - 1)
+    rng = np.random.default_rng(0)
+    for _ in range(40):
+        u = rng.uniform(-1.8, 1.8, 3) * he
+        inside = np.all(np.abs(u) <= he)
+        d = np.linalg.norm(surf - u, axis=1).min()
+        phi, g = oracle_mod.box_sdf(pose, he, pose[:3] + R @ u)
+        exp = -d if inside else d
+        assert abs(phi - exp) <= step, (u, phi, exp)
+        # gradient = finite difference of the distance
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = 1e-6
+            p1, _ = oracle_mod.box_sdf(pose, he, pose[:3] + R @ u + e)
+            p0, _ = oracle_mod.box_sdf(pose, he, pose[:3] + R @ u - e)
+            assert (p1 - p0) / 2e-6 == pytest.approx(g[a], abs=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 10 and Eq. 17: continuity and slopes
+# ---------------------------------------------------------------------------
+
+def test_smooth_distance_profile(oracle_mod):
+    eta = 0.025
+    for d in [-0.1, -eta - 1e-3, -0.02, -0.01, -1e-9, 0.0, 1e-9, 0.01, 0.3]:
+        v, s = oracle_mod.smooth_distance(d, eta)
+        vp, _ = oracle_mod.smooth_distance(d + 1e-7, eta)
+        vm, _ = oracle_mod.smooth_distance(d - 1e-7, eta)
+        assert (vp - vm) / 2e-7 == pytest.approx(s, abs=2e-6)
+    # continuity of value and slope at 0 and -eta; values fixed by Eq. 10
+    assert oracle_mod.smooth_distance(0.0, eta)[0] == pytest.approx(0.5 * eta)
+    assert oracle_mod.smooth_distance(1e-12, eta)[0] == pytest.approx(0.5 * eta)
+    assert oracle_mod.smooth_distance(-eta, eta) == (0.0, 0.0)
+    assert oracle_mod.smooth_distance(0.2, eta) == (0.2 + 0.5 * eta, 1.0)
+    assert oracle_mod.smooth_distance(-eta / 2, eta)[0] == pytest.approx(0.5 / eta * (eta / 2) ** 2)
+
+
+def test_bound_cost_profile(oracle_mod):
+    lo, hi, e2 = -1.0, 2.0, 0.1
+    assert oracle_mod.bound_cost(lo, lo, hi, e2)[0] == pytest.approx(0.5 * e2)
+    assert oracle_mod.bound_cost(hi, lo, hi, e2)[0] == pytest.approx(0.5 * e2)
+    assert oracle_mod.bound_cost(0.5, lo, hi, e2) == (0.0, 0.0)
+    assert oracle_mod.bound_cost(lo - 0.3, lo, hi, e2)[0] == pytest.approx(0.3 + 0.05)
+    assert oracle_mod.bound_cost(hi + 0.3, lo, hi, e2)[0] == pytest.approx(0.3 + 0.05)
+    assert oracle_mod.bound_cost(lo + e2, lo, hi, e2)[0] == pytest.approx(0.0, abs=1e-15)
+    for q in np.linspace(lo - 0.2, hi + 0.2, 97):
+        v, s = oracle_mod.bound_cost(q, lo, hi, e2)
+        vp, _ = oracle_mod.bound_cost(q + 1e-7, lo, hi, e2)
+        vm, _ = oracle_mod.bound_cost(q - 1e-7, lo, hi, e2)
+        assert (vp - vm) / 2e-7 == pytest.approx(s, abs=1e-5)
+        # symmetric profile about the middle of the range
+        vs, _ = oracle_mod.bound_cost(lo + hi - q, lo, hi, e2)
+        assert v == pytest.approx(vs, abs=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# App. A.5 five-point stencils
+# ---------------------------------------------------------------------------
+
+def test_stencils_exact_on_polynomials(oracle_mod):
+    dt = 0.05
+    H = 20
+    ts = np.arange(H + 5) * dt           # ext indices 0..H+4
+    p4 = lambda t: 0.3 - 0.2 * t + 0.7 * t ** 2 - 0.4 * t ** 3 + 0.9 * t ** 4
+    dp4 = lambda t: -0.2 + 1.4 * t - 1.2 * t ** 2 + 3.6 * t ** 3
+    ddp4 = lambda t: 1.4 - 2.4 * t + 10.8 * t ** 2
+    p3 = lambda t: 0.1 + 0.5 * t - 0.3 * t ** 2 + 2.0 * t ** 3
+    # interior samples only (the padding holds copies, not the polynomial)
+    for poly, checks in [(p4, "va"), (p3, "j")]:
+        ext = poly(ts)
+        q0 = np.array([ext[2]])
+        theta = ext[3:H + 3, None]
+        v, a, j = oracle_mod.stencil(q0, theta, dt)
+        for e in range(4, H + 1):         # samples whose five points are all genuine
+            t = ts[e]
+            k = e - 2
+            if "v" in checks:
+                assert v[k, 0] == pytest.approx(dp4(t), rel=1e-9, abs=1e-9)
+            if "a" in checks:
+                assert a[k, 0] == pytest.approx(ddp4(t), rel=1e-7, abs=1e-7)
+            if "j" in checks:
+                assert j[k, 0] == pytest.approx(12.0, rel=1e-9)
+
+
+def test_constant_trajectory_has_zero_derivatives_and_smoothness(oracle_mod):
+    rb = _robot()
+    q0 = np.linspace(-0.3, 0.3, rb.dof)
+    theta = np.tile(q0, (8, 1))
+    v, a, j = oracle_mod.stencil(q0, theta, 0.05)
+    assert np.abs(v).max() < 1e-12 and np.abs(a).max() < 1e-10 and np.abs(j).max() < 1e-9
+    w = synth.World(pose=np.zeros((0, 7)), half_ext=np.zeros((0, 3)))
+    ee = oracle_mod.goal_pose_from_fk(rb, q0)
+    out = oracle_mod.evaluate(rb, w, q0, ee, theta[None])
+    assert out["terms"][0, 3] < 1e-12         # smoothness
+    assert out["terms"][0, 4] == pytest.approx(0.0, abs=1e-6)  # goal reached
+
+
+def test_padding_ties_boundary_states(oracle_mod):
+    """The first sample sees three copies of the start state, the last sample
+    three copies of theta_H: a step from q0 to q1 at t=1 gives the stencil
+    values of the step function."""
+    dt = 0.1
+    q0 = np.array([0.0])
+    theta = np.ones((6, 1))
+    v, a, j = oracle_mod.stencil(q0, theta, dt)
+    # sample e=2 uses [q0, q0, q0, q1, q1]
+    assert v[0, 0] == pytest.approx((8 - 1) / (12 * dt))
+    assert a[0, 0] == pytest.approx((16 - 1) / (12 * dt * dt))
+    assert j[0, 0] == pytest.approx((-2 + 1) / (2 * dt ** 3))
+    # last sample e=H+2 uses [q_{H-2}, q_{H-1}, q_H, q_H, q_H] = all ones
+    assert v[-1, 0] == 0 and a[-1, 0] == 0 and j[-1, 0] == 0
+
+
+# ---------------------------------------------------------------------------
+# Eq. 9 self-collision
+# ---------------------------------------------------------------------------
+
+def _two_sphere_robot(pairs):
+    ident = np.eye(3, 4).reshape(12)
+    n = 4
+    return synth.Robot(fixed_tf=np.stack([ident] * 4), axis=np.array([2, 2, 2], np.int32),
+                       q_lo=-np.ones(3), q_hi=np.ones(3), v_max=np.ones(3), a_max=np.ones(3),
+                       j_max=np.ones(3), spheres=np.zeros((n, 4)),
+                       sphere_link=np.array([0, 2, 0, 2], np.int32),
+                       pairs=np.asarray(pairs, np.int32))
+
+
+def test_self_penetration_two_spheres(oracle_mod):
+    rb = _two_sphere_robot([[0, 1]])
+    X = np.array([[0.0, 0, 0, 0.1], [0.15, 0.05, 0, 0.08], [5, 5, 5, 0.1], [9, 9, 9, 0.1]])
+    pen, arg, g = oracle_mod.self_penetration(rb, X)
+    d = math.hypot(0.15, 0.05)
+    assert pen == pytest.approx(0.18 - d)
+    assert arg == 0
+    u = np.array([0.15, 0.05, 0]) / d
+    # d pen / d x_i points from i toward j (descent pushes the spheres apart)
+    np.testing.assert_allclose(g[0], u, atol=1e-14)
+    np.testing.assert_allclose(g[1], -u, atol=1e-14)
+    # separated: no penetration, no gradient
+    X[1, :3] = [1.0, 0, 0]
+    pen, arg, g = oracle_mod.self_penetration(rb, X)
+    assert pen == 0.0 and arg == -1 and np.abs(g).max() == 0
+
+
+def test_self_penetration_max_and_tie(oracle_mod):
+    rb = _two_sphere_robot([[0, 1], [2, 3]])
+    # exactly representable coordinates, so the tie is exact
+    X = np.array([[0.0, 0, 0, 0.1], [0.125, 0, 0, 0.1], [4, 4, 4, 0.1], [4.125, 4, 4, 0.1]])
+    pen, arg, _ = oracle_mod.self_penetration(rb, X)
+    assert pen == pytest.approx(0.075) and arg == 0        # tie: first in list wins
+    X[3, 0] = 4.0625
+    pen, arg, _ = oracle_mod.self_penetration(rb, X)
+    assert pen == pytest.approx(0.1375) and arg == 1       # max wins
+    X[2, 3] = -1.0                                           # disabled sphere
+    pen, arg, _ = oracle_mod.self_penetration(rb, X)
+    assert arg == 0
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.4 sweep
+# ---------------------------------------------------------------------------
+
+def test_sweep_stationary_reduces_to_discrete(oracle_mod):
+    pose, he = _box(11)
+    rng = np.random.default_rng(4)
+    eta = 0.025
+    for _ in range(30):
+        x = pose[:3] + rng.uniform(-1.5, 1.5, 3) * he
+        r = 0.06
+        S, g, _ = oracle_mod.sweep_box(pose, he, r, x, x, x, eta, 4)
+        phi, gphi = oracle_mod.box_sdf(pose, he, x)
+        dc, slope = oracle_mod.smooth_distance(r - phi, eta)
+        assert S == pytest.approx(dc, abs=1e-15)
+        np.testing.assert_allclose(g, -slope * gphi, atol=1e-14)
+
+
+def test_sweep_detects_thin_box_between_free_waypoints(oracle_mod):
+    eta, r = 0.025, 0.05
+    pose = np.array([0.0, 0, 0, 1, 0, 0, 0])
+    he = np.array([0.01, 0.5, 0.5])            # thin wall at x = 0
+    x0, x1, x2 = np.array([-0.6, 0, 0]), np.array([-0.3, 0, 0]), np.array([0.3, 0, 0])
+    S_disc, _, _ = oracle_mod.sweep_box(pose, he, r, None, x1, None, eta, 4)
+    assert S_disc == 0.0                        # waypoint alone is free
+    S, g, _ = oracle_mod.sweep_box(pose, he, r, x0, x1, x2, eta, 4)
+    assert S > 0.0                              # crossing found by the forward sweep
+    assert g[0] > 0                             # cost grows toward the wall: descent pushes back
+    # and the backward neighbour alone (moving away) finds nothing
+    S_back, _, _ = oracle_mod.sweep_box(pose, he, r, x0, x1, None, eta, 4)
+    assert S_back == 0.0
+
+
+def test_sweep_march_positions(oracle_mod):
+    """Hand-traced march toward a face: the waypoint is free (clearance 0.2 -
+    r), the first sample lands where the sphere touches, the next ones advance
+    by r + eta; the midpoint bound stops the march."""
+    eta, r = 0.025, 0.05
+    pose = np.array([0.0, 0, 0, 1, 0, 0, 0])
+    he = np.array([0.5, 0.5, 0.5])
+    x1 = np.array([-0.7, 0, 0])                 # phi = 0.2
+    x2 = np.array([-0.7 + 2 * 0.3, 0, 0])       # midpoint 0.3 away
+    S, g, _ = oracle_mod.sweep_box(pose, he, r, None, x1, x2, eta, 4)
+    # samples at u = 0.15 (phi = 0.05, pen = 0 -> d_c = eta/2), then u = 0.225 (> 0.3? no)
+    # u = 0.225: phi = -0.025 inside -> pen = 0.075 -> d_c = 0.075 + eta/2; next u = 0.3 stops
+    exp = 0.5 * eta + (0.075 + 0.5 * eta)
+    assert S == pytest.approx(exp, abs=1e-12)
+    np.testing.assert_allclose(g, [2.0, 0, 0], atol=1e-12)  # two samples, slope 1 each, -grad phi = +x
+
+
+def test_sweep_gradient_equals_rigid_translation_derivative(oracle_mod):
+    """When every sample is in collision the march offsets are fixed (steps of
+    r + eta), so translating the three points together moves every sample with
+    x1: the surrogate gradient is then the exact derivative."""
+    eta, r = 0.025, 0.06
+    pose, he = np.array([0.1, -0.2, 0.05, *_quat_axis_angle([1, 2, 3], 0.4)]), np.array([0.4, 0.35, 0.45])
+    x1 = pose[:3] + np.array([0.05, 0.02, -0.03])
+    x0 = x1 + np.array([-0.2, 0.1, 0.05])
+    x2 = x1 + np.array([0.15, -0.1, 0.1])
+    S, g, _ = oracle_mod.sweep_box(pose, he, r, x0, x1, x2, eta, 4)
+    assert S > 0
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = 1e-6
+        Sp, _, _ = oracle_mod.sweep_box(pose, he, r, x0 + e, x1 + e, x2 + e, eta, 4)
+        Sm, _, _ = oracle_mod.sweep_box(pose, he, r, x0 - e, x1 - e, x2 - e, eta, 4)
+        assert (Sp - Sm) / 2e-6 == pytest.approx(g[a], rel=1e-6, abs=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 14 pose cost
+# ---------------------------------------------------------------------------
+
+def test_goal_cost_closed_forms(oracle_mod):
+    p = oracle_mod.params_default()
+    R = _rot(_quat_axis_angle([0.3, -1, 0.2], 0.8))
+    ee = np.concatenate([R, np.array([[0.2], [0.1], [0.4]])], axis=1).reshape(12)
+    q = oracle_mod._rot_to_quat(R)
+    goal = np.array([0.2, 0.1, 0.4, *q])
+    c, dp, dR = oracle_mod.goal_cost(p, ee, goal)
+    assert c == pytest.approx(0.0, abs=1e-9)
+    assert np.abs(dp).max() < 1e-9
+    # quaternion sign does not matter
+    c2, _, _ = oracle_mod.goal_cost(p, ee, np.array([0.2, 0.1, 0.4, *(-q)]))
+    assert c2 == pytest.approx(c, abs=1e-12)
+    # position error 1/alpha_2 along x: alpha_0 log cosh(1)
+    goal_off = goal.copy()
+    goal_off[0] += 1.0 / p["k_goal_pos"]
+    c3, dp3, _ = oracle_mod.goal_cost(p, ee, goal_off)
+    assert c3 == pytest.approx(p["w_goal_pos"] * math.log(math.cosh(1.0)), rel=1e-12)
+    assert dp3[0] == pytest.approx(-p["w_goal_pos"] * p["k_goal_pos"] * math.tanh(1.0), rel=1e-12)
+    # orientation error of angle phi about any axis: d_q = 1 - cos^2(phi/2) = sin^2(phi/2)
+    phi = 0.3
+    Rg = _rot(_quat_axis_angle([0, 0, 1], phi)) @ R
+    qg = oracle_mod._rot_to_quat(Rg)
+    c4, _, _ = oracle_mod.goal_cost(p, ee, np.array([0.2, 0.1, 0.4, *qg]))
+    dq = math.sin(phi / 2) ** 2
+    assert c4 == pytest.approx(p["w_goal_rot"] * math.log(math.cosh(p["k_goal_rot"] * dq)), rel=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# whole evaluation: finite differences (sweep off; the sweep gradient is a
+# surrogate by design, Sec. 3.4) and invariants
+# ---------------------------------------------------------------------------
+
+def _fd_problem(oracle_mod, n_joints, H, K, seed, flags_off=0):
+    rb = _chain(n_joints, seed=seed)
+    rng = np.random.default_rng(seed)
+    w = synth.World(pose=np.array([[*rng.uniform(-0.2, 0.2, 3),
+                                    *_quat_axis_angle(rng.normal(size=3), 0.7)]
+                                   for _ in range(K)]).reshape(-1, 7),
+                    half_ext=rng.uniform(0.1, 0.25, (K, 3)))
+    qs = synth.uniform_config(rng, rb) * 0.6
+    qg = synth.uniform_config(rng, rb) * 0.6
+    goal = oracle_mod.goal_pose_from_fk(rb, qg)
+    goal[:3] += 0.05
+    th = synth.linear_seeds(rng, rb, qs, qg, 2, H, noise=0.2)
+    return rb, w, qs, goal, th
+
+
+def _fd_check(oracle_mod, rb, w, qs, goal, th, params, h=1e-6, rtol=2e-5):
+    out = oracle_mod.evaluate(rb, w, qs, goal, th, params)
+    g = out["grad"]
+    num = np.zeros_like(th)
+    it = np.nditer(th, flags=["multi_index"])
+    for _ in it:
+        idx = it.multi_index
+        tp, tm = th.copy(), th.copy()
+        tp[idx] += h
+        tm[idx] -= h
+        cp = oracle_mod.evaluate(rb, w, qs, goal, tp, params, want_grad=False)["cost"][idx[0]]
+        cm = oracle_mod.evaluate(rb, w, qs, goal, tm, params, want_grad=False)["cost"][idx[0]]
+        num[idx] = (cp - cm) / (2 * h)
+    for b in range(th.shape[0]):
+        err = np.linalg.norm(num[b] - g[b])
+        assert err <= rtol * np.linalg.norm(num[b]) + 1e-6, (b, err, np.linalg.norm(num[b]))
+    return out
+
+
+@pytest.mark.parametrize("n_joints,H", [(2, 5), (3, 6), (7, 6)])
+def test_gradient_finite_difference_trajopt(oracle_mod, n_joints, H):
+    rb, w, qs, goal, th = _fd_problem(oracle_mod, n_joints, H, 3, seed=n_joints)
+    p = dict(flags=oracle_mod.SPEED | oracle_mod.SELF, dt=0.1)
+    out = _fd_check(oracle_mod, rb, w, qs, goal, th, p)
+    assert (out["terms"][:, 0] > 0).any(), "the world term must be active for this pin"
+
+
+def test_gradient_finite_difference_each_term(oracle_mod):
+    """FD per term: switch all other weights off, so a dropped term cannot
+    hide behind a large one."""
+    rb, w, qs, goal, th = _fd_problem(oracle_mod, 7, 6, 3, seed=21)
+    base = dict(flags=oracle_mod.SPEED | oracle_mod.SELF | oracle_mod.VEL_COST, dt=0.1)
+    zero = dict(w_goal_pos=0.0, w_goal_rot=0.0, w_coll=0.0, w_self=0.0, w_bound=0.0,
+                w_acc=0.0, w_jerk=0.0, w_vel=0.0)
+    for keys in [("w_coll",), ("w_self",), ("w_goal_pos",), ("w_goal_rot",), ("w_bound",),
+                 ("w_acc",), ("w_jerk",), ("w_vel",)]:
+        p = dict(base, **zero)
+        for k in keys:
+            p[k] = oracle_mod.params_default()[k]
+        _fd_check(oracle_mod, rb, w, qs, goal, th, p)
+
+
+def test_gradient_finite_difference_ik(oracle_mod):
+    rb, w, qs, goal, th = _fd_problem(oracle_mod, 7, 1, 4, seed=9)
+    p = dict(flags=oracle_mod.IK_MODE | oracle_mod.SELF)
+    th = np.random.default_rng(2).uniform(rb.q_lo, rb.q_hi, (3, 1, rb.dof)) * 0.5
+    _fd_check(oracle_mod, rb, w, qs, goal, th, p)
+
+
+def test_terms_sum_and_stationary_sphere_has_no_world_cost(oracle_mod):
+    """Eq. 11 scales by the sphere speed: a trajectory that holds the start
+    state inside a box costs nothing in the world term, but is not free."""
+    rb = _robot()
+    q = np.zeros(rb.dof)
+    _, sp, _ = oracle_mod.fk(rb, q)
+    w = synth.World(pose=np.array([[*sp[10, :3], 1, 0, 0, 0]]), half_ext=np.full((1, 3), 0.1))
+    th = np.tile(q, (1, 5, 1))
+    out = oracle_mod.evaluate(rb, w, q, np.array([0, 0, 1.0, 1, 0, 0, 0]), th)
+    assert out["terms"][0, 0] == 0.0
+    assert not out["cfree"][0]
+    assert out["cost"][0] == pytest.approx(out["terms"][0].sum(), rel=1e-15)
+    # moving through the same box costs
+    th2 = th.copy()
+    th2[0, 2:, 0] += 0.3
+    out2 = oracle_mod.evaluate(rb, w, q, np.array([0, 0, 1.0, 1, 0, 0, 0]), th2)
+    assert out2["terms"][0, 0] > 0
+
+
+def test_free_flag_against_brute_force(oracle_mod):
+    rb = _robot()
+    rng = np.random.default_rng(8)
+    qs = synth.uniform_config(rng, rb)
+    w = synth.make_world(6, 2)
+    th = synth.linear_seeds(rng, rb, qs, synth.uniform_config(rng, rb), 6, 8)
+    out = oracle_mod.evaluate(rb, w, qs, np.array([0, 0, 1.0, 1, 0, 0, 0]), th)
+    for b in range(6):
+        free = True
+        for t in range(8):
+            _, sp, _ = oracle_mod.fk(rb, th[b, t])
+            for i in range(rb.n_spheres):
+                for k in range(w.n):
+                    phi, _ = oracle_mod.box_sdf(w.pose[k], w.half_ext[k], sp[i, :3])
+                    free &= phi - sp[i, 3] > 0
+            for i, j in rb.pairs:
+                free &= np.linalg.norm(sp[i, :3] - sp[j, :3]) - sp[i, 3] - sp[j, 3] > 0
+        assert bool(out["cfree"][b]) == bool(free)
+
+
+# ---------------------------------------------------------------------------
+# L-BFGS two-loop (App. A.7) and line search (Alg. 1)
+# ---------------------------------------------------------------------------
+
+def _dense_bfgs_direction(S, Y, g):
+    """Explicit BFGS inverse-Hessian recursion H+ = (I - rho s y^T) H (I - rho y s^T) + rho s s^T
+    from H0 = gamma I, over the valid pairs oldest to newest."""
+    n = g.size
+    valid = [(s, y) for s, y in zip(S, Y) if y @ s > 1e-8]
+    if not valid:
+        return -g
+    s_new, y_new = valid[-1]
+    H = (s_new @ y_new) / (y_new @ y_new) * np.eye(n)
+    for s, y in valid:
+        rho = 1.0 / (y @ s)
+        V = np.eye(n) - rho * np.outer(y, s)
+        H = V.T @ H @ V + rho * np.outer(s, s)
+    return -H @ g
+
+
+def test_two_loop_equals_dense_bfgs(oracle_mod):
+    rng = np.random.default_rng(0)
+    n, m = 12, 6
+    A = rng.normal(size=(n, n))
+    A = A @ A.T + n * np.eye(n)
+    st = oracle_mod.LbfgsState(n, m)
+    x = rng.normal(size=n)
+    S, Y = [], []
+    for k in range(9):
+        st.x[:] = x
+        st.g[:] = A @ x + 0.1 * np.sin(x)        # mildly non-quadratic
+        d = st.direction()
+        if k > 0:
+            S.append(x - xp)
+            Y.append(st.g - gp)
+        ref = _dense_bfgs_direction(S[-m:], Y[-m:], st.g)
+        np.testing.assert_allclose(d, ref, rtol=1e-10, atol=1e-12)
+        assert d @ st.g < 0                        # descent
+        xp, gp = x.copy(), st.g.copy()
+        x = x + 0.3 * d
+
+
+def test_two_loop_secant_condition(oracle_mod):
+    """BFGS keeps H y = s for the newest pair: feeding g = y_newest gives d = -s."""
+    rng = np.random.default_rng(1)
+    n, m = 8, 4
+    A = np.diag(rng.uniform(1, 5, n))
+    st = oracle_mod.LbfgsState(n, m)
+    x = rng.normal(size=n)
+    for k in range(5):
+        st.x[:] = x
+        st.g[:] = A @ x
+        d = st.direction()
+        x = x + 0.5 * d
+    # one more update with the new point, then probe with g := y_newest
+    st.x[:] = x
+    st.g[:] = A @ x
+    st.direction()
+    s_new, y_new = st.s[-1].copy(), st.y[-1].copy()
+    probe = oracle_mod.LbfgsState(n, m)
+    probe.s[:], probe.y[:], probe.rho[:] = st.s, st.y, st.rho
+    probe.g[:] = y_new
+    probe.iter[0] = 0                                 # no further history update
+    d = probe.direction()
+    np.testing.assert_allclose(d, -s_new, rtol=1e-10, atol=1e-12)
+
+
+def test_two_loop_first_step_and_inert_pair(oracle_mod):
+    n, m = 5, 3
+    st = oracle_mod.LbfgsState(n, m)
+    st.g[:] = np.arange(1, 6.0)
+    np.testing.assert_allclose(st.direction(), -st.g)     # no history: steepest descent
+    # a step with y^T s <= 1e-8 leaves an inert pair: direction is still -g
+    st.x[:] += 1e-6
+    d = st.direction()
+    assert st.rho[-1] == 0.0
+    np.testing.assert_allclose(d, -st.g)
+
+
+def test_line_search_on_quadratic(oracle_mod):
+    """f(x) = a/2 x^2 from x0 with d = -f'(x0): candidate alpha gives
+    f = f0 (1 - a alpha)^2.  Armijo with c1 holds iff (1-a alpha)^2 <= 1 - 2 c1 a alpha;
+    weak Wolfe with c2 holds iff (1 - a alpha) <= c2."""
+    a, x0 = 2.0, 1.5
+    f = lambda x: 0.5 * a * x * x
+    g0 = np.array([a * x0])
+    d = -g0
+    p = dict(alpha=[0.01, 0.1, 0.3, 0.5, 0.9, 1.0], armijo_c1=1e-4, wolfe_c2=0.9)
+    xs = x0 + np.array(p["alpha"]) * d[0]
+    cc = f(xs)
+    cg = (a * xs)[:, None]
+    for wolfe in (False, True):
+        flags = oracle_mod.WOLFE if wolfe else 0
+        idx, _ = oracle_mod.ls_select(dict(p, flags=flags), f(x0), g0, d, cc, cg)
+        exp = 0
+        for l, al in enumerate(p["alpha"]):
+            ok = (1 - a * al) ** 2 <= 1 - 2 * 1e-4 * a * al
+            if wolfe:
+                ok = ok and (1 - a * al) <= 0.9
+            if ok:
+                exp = l
+        assert idx == exp
+    # no candidate passes: fall back to index 0 (the 0.01 step)
+    idx, _ = oracle_mod.ls_select(dict(p, flags=0), f(x0), g0, d, cc + 100.0, cg)
+    assert idx == 0
+
+
+def test_candidates_are_clipped(oracle_mod):
+    p = dict(alpha=[0.5, 2.0])
+    x = np.array([0.0, 0.9, -0.9, 0.0])
+    d = np.array([1.0, 1.0, -1.0, -1.0])
+    cand = oracle_mod.ls_candidates(p, x, d, [-1.0, -2.0], [1.0, 2.0], 2)
+    np.testing.assert_allclose(cand[0], [0.5, 1.4, -1.0, -0.5])
+    np.testing.assert_allclose(cand[1], [1.0, 2.0, -1.0, -2.0])
+
+
+def test_solve_best_cost_never_increases(oracle_mod):
+    rb = _robot()
+    rng = np.random.default_rng(2)
+    qs = synth.uniform_config(rng, rb)
+    w = synth.make_world(3, 9, lambda p, h: oracle_mod.start_collides_with_box(rb, qs, p, h))
+    pr = synth.make_problem(rb, w, 3, 2, 8, lambda q: oracle_mod.goal_pose_from_fk(rb, q), qs)
+    init = oracle_mod.evaluate(rb, w, qs, pr.goal, pr.seeds)["cost"]
+    prev = init
+    for iters in (1, 3, 6):
+        out = oracle_mod.solve(rb, w, qs, pr.goal, pr.seeds, iters)
+        assert np.all(out["cost"] <= prev + 1e-9)
+        prev = out["cost"]
+        ev = oracle_mod.evaluate(rb, w, qs, pr.goal, out["x"])
+        np.testing.assert_allclose(ev["cost"], out["cost"], rtol=1e-12)
+    assert np.all(prev < init)
