@@ -1,0 +1,218 @@
+/*
+ * crgb.h -- C ABI of the GB300 (sm_103a) library for batched collision-free
+ * trajectory optimisation after "cuRobo: Parallelized Collision-Free
+ * Minimum-Jerk Robot Motion Generation" (arXiv 2310.17274).
+ *
+ * The library evaluates, for every seed x timestep of a batch of joint-space
+ * trajectories, forward kinematics of a serial revolute chain to collision
+ * spheres, sphere-vs-oriented-box signed distance with the swept check and the
+ * speed metric, self-collision, five-point-stencil smoothness, joint-limit and
+ * goal-pose costs, and the backward pass to joint gradients (Sec. 2-3,
+ * App. A); it runs the L-BFGS two-loop step and the parallel noisy line search
+ * on the device (Sec. 4.1, Alg. 1).
+ *
+ * Conventions
+ *  - Every function is `extern "C"`, returns a cr_status and never throws.
+ *    On failure the thread-local message of cr_last_error() says why.
+ *  - "host" pointers are read during the call only (descriptors are copied);
+ *    "device" pointers are CUDA device memory owned by the caller, who keeps
+ *    it alive until the stream has finished the call's work.
+ *  - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream) and is complete when that stream is; calls return before the GPU
+ *    finishes unless stated.
+ *  - Arrays are dense, row-major, float32 unless stated.
+ *  - Sizes: 1 <= dof <= 16, 1 <= spheres <= 1024, pairs <= 65535,
+ *    boxes <= 4096 per world, 1 <= horizon <= 128, history <= 16,
+ *    1 <= n_alpha <= 16.  Anything else returns CR_EINVAL.
+ */
+#ifndef CRGB_H
+#define CRGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t cr_status;
+#define CR_OK 0
+#define CR_EINVAL 1    /* bad argument or size */
+#define CR_ENOMEM 2    /* device or host allocation failed */
+#define CR_ECUDA 3     /* a CUDA call failed (message has the CUDA error) */
+#define CR_ETIMEOUT 4  /* a bounded device wait gave up */
+#define CR_EBUSY 5     /* admission refused: not enough free device memory */
+#define CR_ENAN 6      /* a seed produced a non-finite cost */
+
+#define CR_MAX_DOF 16
+#define CR_MAX_ALPHA 16
+#define CR_MAX_HISTORY 16
+#define CR_N_TERMS 5   /* world, self, bound, smoothness, goal */
+
+/* flags of cr_params.flags */
+#define CR_SWEPT 1u          /* continuous (swept) collision check, Sec. 3.4 */
+#define CR_SPEED 2u          /* speed metric on the world term, Sec. 3.3 / Eq. 11 */
+#define CR_SELF 4u           /* self-collision term, Eq. 9 */
+#define CR_WOLFE 8u          /* Wolfe condition in the line search, Alg. 1 */
+#define CR_STRONG_WOLFE 16u  /* strong Wolfe instead of weak */
+#define CR_IK_MODE 32u       /* single-state problems: no stencil terms, no sweep, no speed */
+#define CR_VEL_COST 64u      /* velocity log-cosh term of Eq. 16 on every sample */
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* cr_last_error(void);
+/* Library version string. */
+const char* cr_version(void);
+
+/* ------------------------------------------------------------------------- */
+/* Robot: serial revolute chain + sphere model (Sec. 3.1; App. E.1 "kinematics
+ * data").  All pointers are host memory, copied to the device at creation.   */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t dof;
+  const float* fixed_tf;      /* [dof+1][12] row-major 3x4 [R|p]: F_0..F_{dof-1}, then F_ee */
+  const int32_t* axis;        /* [dof] revolute axis of each joint: 0 = x, 1 = y, 2 = z */
+  const float* q_lo;          /* [dof] position limits (q_lo < q_hi) */
+  const float* q_hi;          /* [dof] */
+  const float* v_max;         /* [dof] symmetric velocity limit (> 0) */
+  const float* a_max;         /* [dof] symmetric acceleration limit (> 0) */
+  const float* j_max;         /* [dof] symmetric jerk limit (> 0) */
+  int32_t n_spheres;
+  const float* spheres;       /* [M][4] centre in its link frame, radius; radius < 0 disables it */
+  const int32_t* sphere_link; /* [M] link (= joint) index 0..dof-1 the sphere rides on */
+  int32_t n_pairs;
+  const int32_t* pairs;       /* [P][2] self-collision pair set S of Eq. 9, i != j */
+} cr_robot_desc;
+
+typedef struct cr_robot cr_robot;
+/* Copies the description to the device (synchronous).  *out is owned by the
+ * caller and released with cr_robot_destroy. */
+cr_status cr_robot_create(const cr_robot_desc* desc, cr_robot** out);
+void cr_robot_destroy(cr_robot* robot);
+
+/* ------------------------------------------------------------------------- */
+/* World: oriented boxes (Sec. 3.5 "Oriented Bounding Box").                  */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t n;                  /* number of boxes, 0..4096 */
+  const float* pose;          /* [n][7] host: centre xyz, quaternion wxyz (normalised on input) */
+  const float* half_ext;      /* [n][3] host: half extents, each > 0 */
+} cr_world_desc;
+
+typedef struct cr_world cr_world;
+/* Packs the boxes for the device (synchronous copy). */
+cr_status cr_world_create(const cr_world_desc* desc, cr_world** out);
+void cr_world_destroy(cr_world* world);
+
+/* ------------------------------------------------------------------------- */
+/* Parameters (App. A.1-A.3, App. B.3, Sec. 7.3).                              */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  float w_goal_pos, w_goal_rot;  /* alpha_0, alpha_1 of Eq. 14 */
+  float k_goal_pos, k_goal_rot;  /* alpha_2, alpha_3 of Eq. 14 */
+  float w_coll;                  /* beta_2 of Eq. 11 */
+  float w_self;                  /* beta_1 of Eq. 9 */
+  float w_bound;                 /* weight of the Eq. 17 terms */
+  float w_acc, w_jerk;           /* alpha_8, alpha_9 of Eq. 16 */
+  float w_vel, k_vel;            /* alpha_6, alpha_7 of Eq. 16 (with CR_VEL_COST) */
+  float eta;                     /* activation distance of Eq. 10 [m] */
+  float eta_bound;               /* eta_2 of Eq. 17 */
+  float dt;                      /* time step [s] */
+  int32_t sweep_steps;           /* samples per side of the sweep, Sec. 3.4 */
+  int32_t history;               /* L-BFGS memory m, 1..16 */
+  int32_t n_alpha;               /* number of line-search step sizes, 1..16 */
+  float alpha[CR_MAX_ALPHA];     /* step sizes; alpha[0] is the fallback "noisy" step */
+  float armijo_c1, wolfe_c2;
+  uint32_t flags;                /* CR_* flags above */
+} cr_params;
+
+/* Defaults: the paper's weights and constants (App. A.1-A.3, App. B.3:
+ * eta = 2.5 cm, weight 5000 for soft constraints; Sec. 7.3 step sizes
+ * 0.01, 0.3, 0.7, 1.0), dt = 0.05, sweep_steps = 4, history = 6,
+ * c1 = 1e-4, c2 = 0.9, flags = SWEPT|SPEED|SELF|WOLFE. */
+void cr_params_default(cr_params* p);
+
+/* One planning problem (Sec. 2): start configuration, goal pose, world. */
+typedef struct {
+  const cr_world* world;
+  const float* q_start;       /* [dof] host */
+  const float* goal;          /* [7] host: goal position xyz, quaternion wxyz */
+  int32_t n_seeds;            /* B */
+  int32_t horizon;            /* H free timesteps theta_1..theta_H */
+  const float* seeds;         /* [B][H][dof] host initial trajectories (cr_solve only) */
+} cr_problem;
+
+/* ------------------------------------------------------------------------- */
+/* Hot-path primitives                                                        */
+/* ------------------------------------------------------------------------- */
+
+/* Forward kinematics (Sec. 3.1; App. E.1 Table "Joint Transformation
+ * matrices"): for N configurations theta (device [N][dof]) writes the sphere
+ * centres and radii in the world (device [N][M][4], or NULL), the end-effector
+ * pose as a 3x4 [R|p] (device [N][12], or NULL) and the link transforms
+ * T_0..T_{dof-1} (device [N][dof][12], or NULL). */
+cr_status cr_fk(const cr_robot* robot, const float* theta, int32_t n, float* spheres, float* ee,
+                float* link_tf, void* stream);
+
+/* Cost and gradient of B trajectories of one problem (Eq. 1 with every
+ * constraint as a weighted soft cost: Eq. 9, 11, 14, 16, 17).
+ *   theta  device [B][H][dof], H = problem->horizon (problem->seeds unused)
+ *   cost   device [B] total cost
+ *   grad   device [B][H][dof] d cost / d theta, or NULL
+ *   cfree  device [B] uint8: 1 when every waypoint is clear of every box and
+ *          every pair of S is separated (discrete check), or NULL
+ *   terms  device [B][5] world, self, bound, smoothness, goal, or NULL
+ * One fused kernel launch; link transforms stay on chip between the forward
+ * and backward passes.  Deterministic: a trajectory's results do not depend
+ * on B or on the other trajectories. */
+cr_status cr_eval(const cr_robot* robot, const cr_problem* problem, const cr_params* params,
+                  const float* theta, int32_t B, float* cost, float* grad, uint8_t* cfree,
+                  float* terms, void* stream);
+
+/* Device-resident optimiser state of B seeds with n = H*dof variables each
+ * (Sec. 4.1, App. A.7).  Every pointer is device memory owned by the caller.
+ * History buffers hold the newest pair last (index m-1); zeroed buffers with
+ * rho = 0 are inert.  cand* hold the n_alpha line-search candidates of each
+ * seed, seed-major ([B][n_alpha][...]). */
+typedef struct {
+  int32_t n_seeds, horizon;
+  float* x;             /* [B][n] current iterate */
+  float* g;             /* [B][n] its gradient */
+  float* c;             /* [B] its cost */
+  float* x_prev;        /* [B][n] */
+  float* g_prev;        /* [B][n] */
+  float* s;             /* [B][m][n] */
+  float* y;             /* [B][m][n] */
+  float* rho;           /* [B][m] */
+  int32_t* iter;        /* [B] iterations taken (0 = no previous iterate) */
+  float* dir;           /* [B][n] last direction */
+  float* cand;          /* [B][n_alpha][n] */
+  float* cand_cost;     /* [B][n_alpha] */
+  float* cand_grad;     /* [B][n_alpha][n] */
+  uint8_t* cand_cfree;  /* [B][n_alpha] */
+  float* best_x;        /* [B][n] best iterate so far */
+  float* best_c;        /* [B] */
+  uint8_t* best_cfree;  /* [B] */
+  int32_t* ls_index;    /* [B] index chosen by the last line search */
+} cr_opt_state;
+
+/* L-BFGS step (App. A.7 "L-BFGS Step Update"): if iter > 0 append the pair
+ * (x - x_prev, g - g_prev) with rho = 1/(y^T s) when y^T s > 1e-8 else 0,
+ * dropping the oldest; store x_prev = x, g_prev = g; two-loop recursion with
+ * H^0 = gamma I (gamma = s^T y / y^T y of the newest pair with rho > 0, else
+ * 1) gives dir = -H g; then the candidates of Alg. 1,
+ * cand[l] = clip(x + alpha_l dir, q_lo, q_hi).  One CTA per seed. */
+cr_status cr_opt_propose(const cr_robot* robot, const cr_params* params, const cr_opt_state* st,
+                         void* stream);
+
+/* Line search selection of Alg. 1 over evaluated candidates: Armijo
+ * c_l <= c + c1 alpha_l g^T dir (and, with CR_WOLFE, g_l^T dir >= c2 g^T dir,
+ * or |g_l^T dir| <= c2 |g^T dir| with CR_STRONG_WOLFE); the largest passing
+ * index, else 0, becomes (x, g, c); the best iterate is updated when c falls
+ * below best_c (Sec. 4.1).  One CTA per seed. */
+cr_status cr_opt_select(const cr_robot* robot, const cr_params* params, const cr_opt_state* st,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRGB_H */

@@ -1,0 +1,308 @@
+"""Thin ctypes binding of libcrgb.so (include/crgb.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch provides device memory and the current stream.  There
+is no CPU fallback: loading fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcrgb.so")
+_lock = threading.Lock()
+_lib = None
+
+SWEPT, SPEED, SELF, WOLFE, STRONG_WOLFE, IK_MODE, VEL_COST = 1, 2, 4, 8, 16, 32, 64
+N_TERMS = 5
+MAX_ALPHA = 16
+
+_fp = C.POINTER(C.c_float)
+_ip = C.POINTER(C.c_int32)
+_up = C.POINTER(C.c_uint8)
+_vp = C.c_void_p
+
+
+class CrError(RuntimeError):
+    pass
+
+
+class RobotDesc(C.Structure):
+    _fields_ = [("dof", C.c_int32), ("fixed_tf", _fp), ("axis", _ip), ("q_lo", _fp),
+                ("q_hi", _fp), ("v_max", _fp), ("a_max", _fp), ("j_max", _fp),
+                ("n_spheres", C.c_int32), ("spheres", _fp), ("sphere_link", _ip),
+                ("n_pairs", C.c_int32), ("pairs", _ip)]
+
+
+class WorldDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("pose", _fp), ("half_ext", _fp)]
+
+
+class Params(C.Structure):
+    _fields_ = [("w_goal_pos", C.c_float), ("w_goal_rot", C.c_float),
+                ("k_goal_pos", C.c_float), ("k_goal_rot", C.c_float),
+                ("w_coll", C.c_float), ("w_self", C.c_float), ("w_bound", C.c_float),
+                ("w_acc", C.c_float), ("w_jerk", C.c_float), ("w_vel", C.c_float),
+                ("k_vel", C.c_float), ("eta", C.c_float), ("eta_bound", C.c_float),
+                ("dt", C.c_float), ("sweep_steps", C.c_int32), ("history", C.c_int32),
+                ("n_alpha", C.c_int32), ("alpha", C.c_float * MAX_ALPHA),
+                ("armijo_c1", C.c_float), ("wolfe_c2", C.c_float), ("flags", C.c_uint32)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("world", _vp), ("q_start", _fp), ("goal", _fp), ("n_seeds", C.c_int32),
+                ("horizon", C.c_int32), ("seeds", _fp)]
+
+
+class OptState(C.Structure):
+    _fields_ = [("n_seeds", C.c_int32), ("horizon", C.c_int32),
+                ("x", _vp), ("g", _vp), ("c", _vp), ("x_prev", _vp), ("g_prev", _vp),
+                ("s", _vp), ("y", _vp), ("rho", _vp), ("iter", _vp), ("dir", _vp),
+                ("cand", _vp), ("cand_cost", _vp), ("cand_grad", _vp), ("cand_cfree", _vp),
+                ("best_x", _vp), ("best_c", _vp), ("best_cfree", _vp), ("ls_index", _vp)]
+
+
+# name -> (argtypes, restype); the exported symbols of include/crgb.h
+SIGNATURES = {
+    "cr_last_error": ([], C.c_char_p),
+    "cr_version": ([], C.c_char_p),
+    "cr_params_default": ([C.POINTER(Params)], None),
+    "cr_robot_create": ([C.POINTER(RobotDesc), C.POINTER(_vp)], C.c_int32),
+    "cr_robot_destroy": ([_vp], None),
+    "cr_world_create": ([C.POINTER(WorldDesc), C.POINTER(_vp)], C.c_int32),
+    "cr_world_destroy": ([_vp], None),
+    "cr_fk": ([_vp, _vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int32),
+    "cr_eval": ([_vp, C.POINTER(Problem), C.POINTER(Params), _vp, C.c_int32, _vp, _vp, _vp, _vp,
+                 _vp], C.c_int32),
+    "cr_opt_propose": ([_vp, C.POINTER(Params), C.POINTER(OptState), _vp], C.c_int32),
+    "cr_opt_select": ([_vp, C.POINTER(Params), C.POINTER(OptState), _vp], C.c_int32),
+}
+
+
+def lib():
+    """Load libcrgb.so; raise if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise CrError(f"{LIB_PATH} is missing: build it first "
+                                  "(python -m paper_2310_17274_gb300.build)")
+                L = C.CDLL(LIB_PATH)
+                for name, (argt, rest) in SIGNATURES.items():
+                    fn = getattr(L, name)
+                    fn.argtypes = argt
+                    fn.restype = rest
+                _lib = L
+    return _lib
+
+
+def check(status: int, what: str = "") -> None:
+    if status != 0:
+        msg = lib().cr_last_error().decode()
+        raise CrError(f"{what} failed with status {status}: {msg}")
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _p(a, t=_fp):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise CrError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# handles
+# ---------------------------------------------------------------------------
+
+class Robot:
+    """Device copy of a robot description (fields as in synth.Robot)."""
+
+    def __init__(self, rb):
+        self.dof = int(len(rb.axis))
+        self.n_spheres = int(len(rb.spheres))
+        self.n_pairs = int(len(rb.pairs))
+        keep = [_f32(rb.fixed_tf), _i32(rb.axis), _f32(rb.q_lo), _f32(rb.q_hi), _f32(rb.v_max),
+                _f32(rb.a_max), _f32(rb.j_max), _f32(rb.spheres), _i32(rb.sphere_link),
+                _i32(np.asarray(rb.pairs).reshape(-1, 2))]
+        d = RobotDesc(self.dof, _p(keep[0]), _p(keep[1], _ip), _p(keep[2]), _p(keep[3]),
+                      _p(keep[4]), _p(keep[5]), _p(keep[6]), self.n_spheres, _p(keep[7]),
+                      _p(keep[8], _ip), self.n_pairs, _p(keep[9], _ip))
+        h = _vp()
+        check(lib().cr_robot_create(C.byref(d), C.byref(h)), "cr_robot_create")
+        self.handle = h
+        self.q_lo = np.asarray(rb.q_lo, dtype=np.float64)
+        self.q_hi = np.asarray(rb.q_hi, dtype=np.float64)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.cr_robot_destroy(h)
+            self.handle = None
+
+
+class World:
+    def __init__(self, w):
+        pose = _f32(np.asarray(w.pose).reshape(-1, 7))
+        he = _f32(np.asarray(w.half_ext).reshape(-1, 3))
+        self.n = int(len(pose))
+        d = WorldDesc(self.n, _p(pose), _p(he))
+        h = _vp()
+        check(lib().cr_world_create(C.byref(d), C.byref(h)), "cr_world_create")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.cr_world_destroy(h)
+            self.handle = None
+
+
+def params_default() -> dict:
+    p = Params()
+    lib().cr_params_default(C.byref(p))
+    d = {}
+    for name, _ in Params._fields_:
+        v = getattr(p, name)
+        if name == "alpha":
+            v = [float(x) for x in v][: p.n_alpha]
+        d[name] = v
+    return d
+
+
+def make_params(over: dict | None = None) -> Params:
+    base = params_default()
+    if over:
+        base.update(over)
+    p = Params()
+    for name, _ in Params._fields_:
+        if name == "alpha":
+            al = list(base["alpha"])
+            if len(al) > MAX_ALPHA:
+                raise CrError("too many step sizes")
+            for i, a in enumerate(al):
+                p.alpha[i] = float(a)
+            p.n_alpha = len(al)
+        elif name == "n_alpha":
+            continue
+        else:
+            setattr(p, name, base[name])
+    return p
+
+
+class ProblemSpec:
+    """Host-side arrays of one problem, kept alive for the ctypes struct."""
+
+    def __init__(self, world: World, q_start, goal, horizon: int, seeds=None):
+        self.world = world
+        self.q_start = _f32(q_start)
+        self.goal = _f32(goal)
+        self.horizon = int(horizon)
+        self.seeds = None if seeds is None else _f32(seeds)
+
+    def struct(self) -> Problem:
+        B = 0 if self.seeds is None else int(self.seeds.shape[0])
+        return Problem(self.world.handle, _p(self.q_start), _p(self.goal), B, self.horizon,
+                       _p(self.seeds))
+
+
+# ---------------------------------------------------------------------------
+# hot-path calls
+# ---------------------------------------------------------------------------
+
+def fk(robot: Robot, theta, spheres=True, ee=True, link_tf=False, stream=None):
+    """Forward kinematics of theta (CUDA tensor [N, dof])."""
+    import torch
+    theta = theta.contiguous()
+    n = theta.shape[0]
+    dev = theta.device
+    sp = torch.empty((n, robot.n_spheres, 4), device=dev) if spheres else None
+    e = torch.empty((n, 12), device=dev) if ee else None
+    lt = torch.empty((n, robot.dof, 12), device=dev) if link_tf else None
+    check(lib().cr_fk(robot.handle, _dptr(theta), n, _dptr(sp), _dptr(e), _dptr(lt),
+                      _stream(stream)), "cr_fk")
+    return sp, e, lt
+
+
+def evaluate(robot: Robot, problem: ProblemSpec, theta, params=None, want_grad=True,
+             want_terms=True, stream=None):
+    """Cost, gradient, collision-free flags and per-term costs of theta
+    (CUDA float32 tensor [B, H, dof]) in one fused launch."""
+    import torch
+    theta = theta.contiguous()
+    B = theta.shape[0]
+    dev = theta.device
+    cost = torch.empty(B, device=dev)
+    grad = torch.empty_like(theta) if want_grad else None
+    cfree = torch.empty(B, device=dev, dtype=torch.uint8)
+    terms = torch.empty((B, N_TERMS), device=dev) if want_terms else None
+    P = params if isinstance(params, Params) else make_params(params)
+    pr = problem.struct()
+    check(lib().cr_eval(robot.handle, C.byref(pr), C.byref(P), _dptr(theta), B, _dptr(cost),
+                        _dptr(grad), _dptr(cfree), _dptr(terms), _stream(stream)), "cr_eval")
+    return dict(cost=cost, grad=grad, cfree=cfree, terms=terms)
+
+
+class OptBuffers:
+    """Device-resident optimiser state of B seeds (cr_opt_state), as torch tensors."""
+
+    def __init__(self, n_seeds, horizon, dof, history, n_alpha, device="cuda"):
+        import torch
+        B, n, m, na = n_seeds, horizon * dof, history, n_alpha
+        z = lambda *s, dt=torch.float32: torch.zeros(s, device=device, dtype=dt)
+        self.n_seeds, self.horizon, self.dof, self.m, self.na = B, horizon, dof, m, na
+        self.x, self.g, self.c = z(B, n), z(B, n), z(B)
+        self.x_prev, self.g_prev = z(B, n), z(B, n)
+        self.s, self.y, self.rho = z(B, m, n), z(B, m, n), z(B, m)
+        self.iter = z(B, dt=torch.int32)
+        self.dir = z(B, n)
+        self.cand, self.cand_cost = z(B, na, n), z(B, na)
+        self.cand_grad = z(B, na, n)
+        self.cand_cfree = z(B, na, dt=torch.uint8)
+        self.best_x, self.best_c = z(B, n), z(B)
+        self.best_cfree = z(B, dt=torch.uint8)
+        self.ls_index = z(B, dt=torch.int32)
+
+    def struct(self) -> OptState:
+        f = [_dptr(getattr(self, k)) for k in
+             ("x", "g", "c", "x_prev", "g_prev", "s", "y", "rho", "iter", "dir", "cand",
+              "cand_cost", "cand_grad", "cand_cfree", "best_x", "best_c", "best_cfree",
+              "ls_index")]
+        return OptState(self.n_seeds, self.horizon, *f)
+
+
+def opt_propose(robot: Robot, params, st: OptBuffers, stream=None):
+    P = params if isinstance(params, Params) else make_params(params)
+    s = st.struct()
+    check(lib().cr_opt_propose(robot.handle, C.byref(P), C.byref(s), _stream(stream)),
+          "cr_opt_propose")
+
+
+def opt_select(robot: Robot, params, st: OptBuffers, stream=None):
+    P = params if isinstance(params, Params) else make_params(params)
+    s = st.struct()
+    check(lib().cr_opt_select(robot.handle, C.byref(P), C.byref(s), _stream(stream)),
+          "cr_opt_select")

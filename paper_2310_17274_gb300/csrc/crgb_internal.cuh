@@ -1,0 +1,126 @@
+// crgb_internal.cuh -- device-side views and launch helpers shared by the
+// library's translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/crgb.h"
+
+namespace crgb {
+
+constexpr int kMaxDof = CR_MAX_DOF;
+constexpr int kMaxSpheres = 1024;
+constexpr int kMaxPairs = 65535;
+constexpr int kMaxBoxes = 4096;
+constexpr int kMaxHorizon = 128;
+constexpr int kBoxChunk = 64;  // boxes staged in shared memory at a time
+
+// Robot as the kernels see it (device pointers into one allocation).
+struct RobotView {
+  int dof, n_spheres, n_pairs;
+  const float* fixed_tf;    // [(dof+1)*12]
+  const int* axis;          // [dof]
+  const float* lim;         // [5][dof]: q_lo, q_hi, v_max, a_max, j_max
+  const float4* spheres;    // [M] centre (link frame), radius
+  const int* sphere_link;   // [M]
+  const uint32_t* pairs;    // [P] i | (j << 16)
+};
+
+// One box packed as four float4 rows: (R^T row k, t_k) for k = 0..2 so that
+// u = R^T x + t is the point in the box frame, then (half extents, |h|).
+struct BoxRows {
+  float4 r0, r1, r2, h;
+};
+
+// One problem of a batch.
+struct ProblemView {
+  const BoxRows* boxes;
+  int n_boxes;
+  int horizon;
+  int n_traj;          // trajectories of this problem in the evaluated batch
+  int traj_base;       // index of its first trajectory in cost/cfree/terms
+  long long var_base;  // float offset of its first trajectory in theta/grad
+  float q_start[kMaxDof];
+  float goal_p[3];
+  float goal_R[9];     // row-major
+};
+
+// Arguments of the fused evaluation kernel.
+struct EvalArgs {
+  RobotView rb;
+  cr_params prm;
+  ProblemView prob0;             // single-problem launch
+  const ProblemView* problems;   // batched launch: device table, or nullptr
+  const int4* tiles;             // batched launch: (problem, first traj, n traj, -)
+  int n_tiles;
+  int traj_per_tile;             // single-problem launch: trajectories per CTA
+  int max_traj;                  // largest trajectory count of a tile
+  int max_states;                // largest (trajectories x horizon) of a tile
+  int max_horizon;
+  const float* theta;
+  float* cost;
+  float* grad;
+  uint8_t* cfree;
+  float* terms;
+};
+
+// Shared-memory carve-up of the evaluation kernel (host and device agree).
+struct EvalSmem {
+  int off_fix, off_lim, off_sph, off_link, off_pairs, off_th, off_lt, off_sg, off_stw, off_sts,
+      off_sta, off_gth, off_wsph, off_box, off_sten, off_pb, off_db, off_sm, off_goal, off_free,
+      bytes;
+  __host__ __device__ static int align16(int x) { return (x + 15) & ~15; }
+  __host__ __device__ void build(int dof, int M, int P, int max_traj, int max_states,
+                                 int max_horizon, int n_warps) {
+    int o = 0;
+    auto take = [&](int nbytes) { int r = o; o = align16(o + nbytes); return r; };
+    off_fix = take((dof + 1) * 12 * 4);
+    off_lim = take(5 * dof * 4);
+    off_sph = take(M * 16);
+    off_link = take(M * 4);
+    off_pairs = take(P * 4);
+    off_th = take(max_states * dof * 4);
+    off_lt = take((1 + max_states) * dof * 12 * 4);
+    off_sg = take(max_states * M * 16);
+    off_stw = take(max_states * 4);
+    off_sts = take(max_states * 4);
+    off_sta = take(max_states * 4);
+    off_gth = take(max_states * dof * 4);
+    off_wsph = take(n_warps * M * 16);
+    off_box = take(kBoxChunk * 64);
+    int n_samples = max_traj * (max_horizon + 1) * dof;
+    off_sten = take(n_samples * 3 * 4);
+    off_pb = take(max_states * dof * 4);
+    off_db = take(n_samples * 4);
+    off_sm = take(n_samples * 4);
+    off_goal = take(max_traj * 4);
+    off_free = take(max_traj * 4);
+    bytes = o;
+  }
+};
+
+// Arguments of the optimiser kernels (one CTA per seed).
+struct OptArgs {
+  cr_params prm;
+  const float* q_lo;   // device [dof]
+  const float* q_hi;
+  int dof;
+  int n_seeds;
+  int horizon;         // uniform horizon (single problem), or 0 with seed table
+  const int4* seed_tab;  // batched: per seed (n vars, var offset, cand offset, problem), or nullptr
+  cr_opt_state st;
+  int do_select;
+  int do_propose;
+  int init_best;       // first call after the initial evaluation: best := current
+};
+
+// launch helpers (k_eval.cu / k_opt.cu)
+cudaError_t launch_fk(const RobotView& rb, const float* theta, int n, float* spheres, float* ee,
+                      float* link_tf, cudaStream_t stream);
+cudaError_t launch_eval(const EvalArgs& a, int grid, int block, cudaStream_t stream);
+int eval_smem_bytes(const EvalArgs& a, int block);
+cudaError_t launch_opt(const OptArgs& a, int n_max, cudaStream_t stream);
+int opt_smem_bytes(int history, int n_max);
+
+}  // namespace crgb

@@ -1,0 +1,708 @@
+// k_eval.cu -- fused cost-and-gradient evaluation over seeds x timesteps, and
+// forward kinematics, for sm_103a.
+//
+// One CTA owns a tile of whole trajectories of one problem: a single
+// trajectory for trajectory optimisation (H = 32..128 states), or a group of
+// single-state trajectories for IK.  Everything a trajectory needs stays on
+// chip: the link transforms of every state (forward kinematics, Sec. 3.1),
+// the per-(state, sphere) swept world sums and their gradients (Sec. 3.3-3.4,
+// Eq. 10-11), the self-collision argmax per state (Eq. 9), the stencil
+// derivatives (App. A.5) and the joint gradients.  Only theta is read from
+// HBM and only cost / gradient / flags are written back.
+//
+// Work mapping inside a tile: a warp owns a state, a lane owns spheres
+// (i = lane, lane + 32, ...).  Boxes are staged in shared memory in chunks and
+// read as warp-wide broadcasts; a cheap squared-distance test skips the
+// (sphere, box) pairs whose sweep cannot reach the box.  Every reduction has a
+// fixed shape (sequential per lane, then an xor butterfly), so a trajectory's
+// result does not depend on the tile size, the CTA size or the other work in
+// the launch.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "crgb_internal.cuh"
+
+namespace crgb {
+
+namespace {
+
+struct V3 {
+  float x, y, z;
+};
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return V3{x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return v3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float norm(V3 a) { return sqrtf(dot(a, a)); }
+
+// point x (link frame centre c) through a row-major 3x4 [R|p]
+__device__ __forceinline__ V3 tf_point(const float* T, float cx, float cy, float cz) {
+  return v3(fmaf(T[0], cx, fmaf(T[1], cy, fmaf(T[2], cz, T[3]))),
+            fmaf(T[4], cx, fmaf(T[5], cy, fmaf(T[6], cz, T[7]))),
+            fmaf(T[8], cx, fmaf(T[9], cy, fmaf(T[10], cz, T[11]))));
+}
+
+// Serial chain (Sec. 3.1): T_j = T_{j-1} F_j J_axis(theta_j), where F_j J is
+// the "full link transformation" of App. E.1's joint table (two columns of F
+// mixed by cos / sin).  Writes T_0..T_{dof-1} (12 floats each).
+__device__ __forceinline__ void fk_chain(const float* fix, const int* axis, int dof,
+                                         const float* q, float* out) {
+  float T[12] = {1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f};
+  for (int j = 0; j < dof; ++j) {
+    const float* F = fix + 12 * j;
+    float s, c;
+    sincosf(q[j], &s, &c);
+    float A[12];
+    const int ax = axis[j];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      float f0 = F[4 * r], f1 = F[4 * r + 1], f2 = F[4 * r + 2];
+      if (ax == 0) {
+        A[4 * r] = f0;
+        A[4 * r + 1] = fmaf(f1, c, f2 * s);
+        A[4 * r + 2] = fmaf(-f1, s, f2 * c);
+      } else if (ax == 1) {
+        A[4 * r] = fmaf(f0, c, -f2 * s);
+        A[4 * r + 1] = f1;
+        A[4 * r + 2] = fmaf(f0, s, f2 * c);
+      } else {
+        A[4 * r] = fmaf(f0, c, f1 * s);
+        A[4 * r + 1] = fmaf(-f0, s, f1 * c);
+        A[4 * r + 2] = f2;
+      }
+      A[4 * r + 3] = F[4 * r + 3];
+    }
+    float N[12];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+      for (int col = 0; col < 4; ++col) {
+        float v = fmaf(T[4 * r], A[col], fmaf(T[4 * r + 1], A[4 + col], T[4 * r + 2] * A[8 + col]));
+        N[4 * r + col] = col == 3 ? v + T[4 * r + 3] : v;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      T[k] = N[k];
+      out[12 * j + k] = N[k];
+    }
+  }
+}
+
+// Box signed distance in the box frame (textbook: Euclidean outside, minus
+// the smallest face gap inside) and its gradient in the box frame; inside,
+// the face of the largest q wins, lowest axis on ties.
+__device__ __forceinline__ float sdf_local(float ux, float uy, float uz, float4 h, V3& gu) {
+  float qx = fabsf(ux) - h.x, qy = fabsf(uy) - h.y, qz = fabsf(uz) - h.z;
+  float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
+  float outside = sqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz)));
+  int a = 0;
+  float mq = qx;
+  if (qy > mq) { a = 1; mq = qy; }
+  if (qz > mq) { a = 2; mq = qz; }
+  float sx = ux >= 0.f ? 1.f : -1.f, sy = uy >= 0.f ? 1.f : -1.f, sz = uz >= 0.f ? 1.f : -1.f;
+  if (outside > 0.f) {
+    float inv = 1.f / outside;
+    gu = v3(sx * mx * inv, sy * my * inv, sz * mz * inv);
+  } else {
+    gu = v3(a == 0 ? sx : 0.f, a == 1 ? sy : 0.f, a == 2 ? sz : 0.f);
+  }
+  return outside + fminf(mq, 0.f);
+}
+
+// Eq. 10 smoothed collision distance and its slope
+__device__ __forceinline__ float smooth_dist(float d, float eta, float inv_eta, float& slope) {
+  if (d > 0.f) {
+    slope = 1.f;
+    return d + 0.5f * eta;
+  }
+  if (d > -eta) {
+    float e = d + eta;
+    slope = e * inv_eta;
+    return 0.5f * inv_eta * e * e;
+  }
+  slope = 0.f;
+  return 0.f;
+}
+
+// Eq. 17 bound cost and slope
+__device__ __forceinline__ float bound_cost(float q, float lo, float hi, float e2, float inv_e2,
+                                            float& s) {
+  if (q < lo) { s = -1.f; return lo - q + 0.5f * e2; }
+  if (q < lo + e2) { float d = lo - q + e2; s = -d * inv_e2; return 0.5f * inv_e2 * d * d; }
+  if (q > hi) { s = 1.f; return q - hi + 0.5f * e2; }
+  if (q > hi - e2) { float d = q - hi + e2; s = d * inv_e2; return 0.5f * inv_e2 * d * d; }
+  s = 0.f;
+  return 0.f;
+}
+
+__device__ __forceinline__ float logcoshf(float x) {
+  float a = fabsf(x);
+  return a + log1pf(expf(-2.f * a)) - 0.69314718055994531f;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// penetration test sample in the box frame: accumulates S and the box-frame
+// gradient of S w.r.t. the sample (d pen / d u = -grad phi)
+struct SweepAcc {
+  float S;
+  V3 g;
+};
+
+__device__ __forceinline__ float sample_pen(const BoxRows& b, float ux, float uy, float uz, float r,
+                                            float eta, float inv_eta, SweepAcc& acc, bool& hit) {
+  V3 gu;
+  float phi = sdf_local(ux, uy, uz, b.h, gu);
+  float pen = r - phi;
+  hit = pen > -eta;
+  if (hit) {
+    float sl;
+    acc.S += smooth_dist(pen, eta, inv_eta, sl);
+    acc.g = acc.g - sl * gu;
+  }
+  return phi;
+}
+
+template <int DMAX>
+__global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ProblemView s_prob;
+  __shared__ int s_axis[kMaxDof];
+
+  const int D = a.rb.dof, M = a.rb.n_spheres, P = a.rb.n_pairs;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+  const cr_params& prm = a.prm;
+  const uint32_t flags = prm.flags;
+  const bool ik = (flags & CR_IK_MODE) != 0;
+  const bool swept = !ik && (flags & CR_SWEPT);
+  const bool speed = !ik && (flags & CR_SPEED);
+  const bool selfc = (flags & CR_SELF) != 0;
+  const float eta = prm.eta, inv_eta = 1.f / prm.eta;
+  const float e2 = prm.eta_bound, inv_e2 = 1.f / prm.eta_bound;
+  const float dt = prm.dt, inv2dt = 0.5f / dt;
+
+  EvalSmem L;
+  L.build(D, M, P, a.max_traj, a.max_states, a.max_horizon, nw);
+  float* s_fix = reinterpret_cast<float*>(smem + L.off_fix);
+  float* s_lim = reinterpret_cast<float*>(smem + L.off_lim);
+  float4* s_sph = reinterpret_cast<float4*>(smem + L.off_sph);
+  int* s_link = reinterpret_cast<int*>(smem + L.off_link);
+  uint32_t* s_pairs = reinterpret_cast<uint32_t*>(smem + L.off_pairs);
+  float* s_th = reinterpret_cast<float*>(smem + L.off_th);
+  float* s_lt = reinterpret_cast<float*>(smem + L.off_lt);
+  float4* s_sg = reinterpret_cast<float4*>(smem + L.off_sg);
+  float* s_stw = reinterpret_cast<float*>(smem + L.off_stw);
+  float* s_sts = reinterpret_cast<float*>(smem + L.off_sts);
+  int* s_sta = reinterpret_cast<int*>(smem + L.off_sta);
+  float* s_gth = reinterpret_cast<float*>(smem + L.off_gth);
+  float4* s_wsph = reinterpret_cast<float4*>(smem + L.off_wsph);
+  BoxRows* s_box = reinterpret_cast<BoxRows*>(smem + L.off_box);
+  float* s_sten = reinterpret_cast<float*>(smem + L.off_sten);
+  float* s_pb = reinterpret_cast<float*>(smem + L.off_pb);
+  float* s_db = reinterpret_cast<float*>(smem + L.off_db);
+  float* s_sm = reinterpret_cast<float*>(smem + L.off_sm);
+  float* s_goal = reinterpret_cast<float*>(smem + L.off_goal);
+  int* s_free = reinterpret_cast<int*>(smem + L.off_free);
+
+  // robot model, once per CTA
+  for (int k = tid; k < (D + 1) * 12; k += nthr) s_fix[k] = a.rb.fixed_tf[k];
+  for (int k = tid; k < 5 * D; k += nthr) s_lim[k] = a.rb.lim[k];
+  for (int k = tid; k < M; k += nthr) {
+    s_sph[k] = a.rb.spheres[k];
+    s_link[k] = a.rb.sphere_link[k];
+  }
+  for (int k = tid; k < P; k += nthr) s_pairs[k] = a.rb.pairs[k];
+  for (int k = tid; k < D; k += nthr) s_axis[k] = a.rb.axis[k];
+
+  const int n_tiles = a.problems ? a.n_tiles
+                                 : (a.prob0.n_traj + a.traj_per_tile - 1) / a.traj_per_tile;
+
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const ProblemView* pv;
+    int r0, nt;
+    if (a.problems) {
+      int4 td = a.tiles[tile];
+      pv = a.problems + td.x;
+      r0 = td.y;
+      nt = td.z;
+    } else {
+      pv = &a.prob0;
+      r0 = tile * a.traj_per_tile;
+      nt = min(a.traj_per_tile, a.prob0.n_traj - r0);
+    }
+    __syncthreads();  // previous tile fully consumed
+    {
+      const int* src = reinterpret_cast<const int*>(pv);
+      int* dst = reinterpret_cast<int*>(&s_prob);
+      for (int k = tid; k < (int)(sizeof(ProblemView) / 4); k += nthr) dst[k] = src[k];
+    }
+    __syncthreads();
+    const int H = s_prob.horizon;
+    const int K = s_prob.n_boxes;
+    const int S = nt * H;
+    const long long vbase = s_prob.var_base + (long long)r0 * H * D;
+
+    for (int k = tid; k < S * D; k += nthr) s_th[k] = a.theta[vbase + k];
+    for (int k = tid; k < nt; k += nthr) {
+      s_free[k] = 1;
+      s_goal[k] = 0.f;
+    }
+    for (int k = tid; k < S * M; k += nthr) s_sg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+
+    // ---- forward kinematics: slot 0 = start state, slot 1 + sigma = state sigma
+    for (int s = tid; s < 1 + S; s += nthr) {
+      const float* q = s == 0 ? s_prob.q_start : s_th + (s - 1) * D;
+      fk_chain(s_fix, s_axis, D, q, s_lt + s * D * 12);
+    }
+
+    // slot of timestep tt (0 = start, clamped to H) of trajectory r
+    auto slot = [&](int r, int tt) -> int {
+      if (tt <= 0) return 0;
+      if (tt > H) tt = H;
+      return 1 + r * H + tt - 1;
+    };
+    auto sphere_at = [&](int sl, int i) -> V3 {
+      float4 c = s_sph[i];
+      return tf_point(s_lt + (sl * D + s_link[i]) * 12, c.x, c.y, c.z);
+    };
+
+    // ---- world term (Eq. 11 with the sweep of Sec. 3.4), box chunk by box chunk
+    for (int c0 = 0; c0 < K; c0 += kBoxChunk) {
+      const int kc = min(kBoxChunk, K - c0);
+      __syncthreads();
+      {
+        const float4* src = reinterpret_cast<const float4*>(s_prob.boxes + c0);
+        float4* dst = reinterpret_cast<float4*>(s_box);
+        for (int k = tid; k < kc * 4; k += nthr) dst[k] = src[k];
+      }
+      __syncthreads();
+      for (int sg = warp; sg < S; sg += nw) {
+        const int r = sg / H, t = sg % H + 1;
+        for (int i = lane; i < M; i += 32) {
+          const float rad = s_sph[i].w;
+          if (rad < 0.f) continue;
+          const V3 x1 = sphere_at(slot(r, t), i);
+          V3 dir0 = v3(0.f, 0.f, 0.f), dir2 = dir0;
+          float L0 = 0.f, L2 = 0.f;
+          if (swept) {
+            V3 d0 = sphere_at(slot(r, t - 1), i) - x1;
+            V3 d2 = sphere_at(slot(r, t + 1), i) - x1;
+            float n0 = norm(d0), n2 = norm(d2);
+            L0 = 0.5f * n0;
+            L2 = 0.5f * n2;
+            if (n0 > 0.f) dir0 = (1.f / n0) * d0;
+            if (n2 > 0.f) dir2 = (1.f / n2) * d2;
+          }
+          const float rhat = rad + eta;
+          // beyond this clearance neither the waypoint nor a sweep sample can
+          // reach the box: phi >= r + max(eta, L) adds exactly nothing
+          const float thr = rad + fmaxf(eta, fmaxf(L0, L2));
+          const float thr2 = thr * thr;
+          float4 acc4 = s_sg[sg * M + i];
+          bool clear = true;
+          for (int kk = 0; kk < kc; ++kk) {
+            const BoxRows b = s_box[kk];
+            const float ux = fmaf(b.r0.x, x1.x, fmaf(b.r0.y, x1.y, fmaf(b.r0.z, x1.z, b.r0.w)));
+            const float uy = fmaf(b.r1.x, x1.x, fmaf(b.r1.y, x1.y, fmaf(b.r1.z, x1.z, b.r1.w)));
+            const float uz = fmaf(b.r2.x, x1.x, fmaf(b.r2.y, x1.y, fmaf(b.r2.z, x1.z, b.r2.w)));
+            const float mx = fmaxf(fabsf(ux) - b.h.x, 0.f);
+            const float my = fmaxf(fabsf(uy) - b.h.y, 0.f);
+            const float mz = fmaxf(fabsf(uz) - b.h.z, 0.f);
+            if (fmaf(mx, mx, fmaf(my, my, mz * mz)) >= thr2) continue;
+            // slow path: waypoint, then the two half-way sweeps
+            SweepAcc sw{0.f, v3(0.f, 0.f, 0.f)};
+            bool hit;
+            const float phi1 = sample_pen(b, ux, uy, uz, rad, eta, inv_eta, sw, hit);
+            if (!(phi1 - rad > 0.f)) clear = false;
+            const float u0 = hit ? rhat : phi1 - rad;
+            if (swept) {
+#pragma unroll
+              for (int side = 0; side < 2; ++side) {
+                const float Ls = side == 0 ? L0 : L2;
+                if (!(Ls > 0.f)) continue;
+                const V3 dw = side == 0 ? dir0 : dir2;
+                // direction in the box frame (rotation only)
+                const float dx = fmaf(b.r0.x, dw.x, fmaf(b.r0.y, dw.y, b.r0.z * dw.z));
+                const float dy = fmaf(b.r1.x, dw.x, fmaf(b.r1.y, dw.y, b.r1.z * dw.z));
+                const float dz = fmaf(b.r2.x, dw.x, fmaf(b.r2.y, dw.y, b.r2.z * dw.z));
+                float u = u0;
+                for (int st = 0; st < prm.sweep_steps; ++st) {
+                  if (u >= Ls) break;
+                  const float phi = sample_pen(b, fmaf(u, dx, ux), fmaf(u, dy, uy), fmaf(u, dz, uz),
+                                               rad, eta, inv_eta, sw, hit);
+                  u += hit ? rhat : phi - rad;
+                }
+              }
+            }
+            // box frame -> world frame: grad_x = R grad_u, R = (R^T)^T
+            acc4.x += sw.S;
+            acc4.y += fmaf(b.r0.x, sw.g.x, fmaf(b.r1.x, sw.g.y, b.r2.x * sw.g.z));
+            acc4.z += fmaf(b.r0.y, sw.g.x, fmaf(b.r1.y, sw.g.y, b.r2.y * sw.g.z));
+            acc4.w += fmaf(b.r0.z, sw.g.x, fmaf(b.r1.z, sw.g.y, b.r2.z * sw.g.z));
+          }
+          s_sg[sg * M + i] = acc4;
+          if (!clear) s_free[r] = 0;
+        }
+      }
+    }
+
+    // ---- self-collision (Eq. 9): largest penetration over the pair set per state
+    for (int sg = warp; sg < S; sg += nw) {
+      const int r = sg / H, t = sg % H + 1;
+      float4* wsp = s_wsph + warp * M;
+      for (int i = lane; i < M; i += 32) {
+        V3 x = sphere_at(slot(r, t), i);
+        wsp[i] = make_float4(x.x, x.y, x.z, s_sph[i].w);
+      }
+      __syncwarp();
+      float best = 0.f;
+      int arg = -1;
+      bool touch = false;
+      for (int p = lane; p < P; p += 32) {
+        const uint32_t pr = s_pairs[p];
+        const float4 A = wsp[pr & 0xffffu], B = wsp[pr >> 16];
+        if (A.w <= 0.f || B.w <= 0.f) continue;
+        const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float rs = A.w + B.w;
+        const float lim = rs + 1e-3f;
+        if (d2 >= lim * lim) continue;  // separated by more than 1 mm: no effect
+        const float pen = rs - sqrtf(d2);
+        if (!(-pen > 0.f)) touch = true;
+        if (pen > best) {  // lanes visit pairs in increasing order: ties keep the first
+          best = pen;
+          arg = p;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+        if (ob > best || (ob == best && ob > 0.f && oa < arg)) {
+          best = ob;
+          arg = oa;
+        }
+      }
+      touch = __any_sync(0xffffffffu, touch);
+      if (lane == 0) {
+        s_sts[sg] = best;
+        s_sta[sg] = arg;
+        if (touch) s_free[r] = 0;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+
+    // ---- backward: d cost / d sphere centre, then Jacobian-transpose to joints
+    // (App. E.1 Table "Gradient for different joint types": revolute joint j
+    // moves a point x by a_j x (x - o_j), rotates a frame R by [a_j]_x R).
+    for (int sg = warp; sg < S; sg += nw) {
+      const int r = sg / H, t = sg % H + 1;
+      const float* LTt = s_lt + slot(r, t) * D * 12;
+      float acc[DMAX];
+#pragma unroll
+      for (int j = 0; j < DMAX; ++j) acc[j] = 0.f;
+      float wcost = 0.f;
+      const int parg = selfc ? s_sta[sg] : -1;
+      const uint32_t pr = parg >= 0 ? s_pairs[parg] : 0u;
+      const int pi = (int)(pr & 0xffffu), pj = (int)(pr >> 16);
+      for (int i = lane; i < M; i += 32) {
+        const float4 c = s_sph[i];
+        if (c.w < 0.f) continue;
+        const int l = s_link[i];
+        const V3 x = tf_point(LTt + l * 12, c.x, c.y, c.z);
+        V3 gx = v3(0.f, 0.f, 0.f);
+        if (K > 0) {
+          const float4 sgv = s_sg[sg * M + i];
+          float v = 1.f;
+          if (speed) {
+            const V3 d = sphere_at(slot(r, t + 1), i) - sphere_at(slot(r, t - 1), i);
+            const float n = norm(d);
+            v = n * inv2dt;
+            // x_{H+1} := x_H, so the last state's own speed depends on it
+            if (t == H && n > 0.f && sgv.x != 0.f) gx = gx + (prm.w_coll * sgv.x * inv2dt / n) * d;
+            if (t >= 2) {
+              const float Sm = s_sg[(sg - 1) * M + i].x;
+              if (Sm != 0.f) {
+                const V3 dm = x - sphere_at(slot(r, t - 2), i);
+                const float nm = norm(dm);
+                if (nm > 0.f) gx = gx + (prm.w_coll * Sm * inv2dt / nm) * dm;
+              }
+            }
+            if (t + 1 <= H) {
+              const float Sp = s_sg[(sg + 1) * M + i].x;
+              if (Sp != 0.f) {
+                const V3 dp = sphere_at(slot(r, t + 2), i) - x;
+                const float np = norm(dp);
+                if (np > 0.f) gx = gx - (prm.w_coll * Sp * inv2dt / np) * dp;
+              }
+            }
+          }
+          gx = gx + (prm.w_coll * v) * v3(sgv.y, sgv.z, sgv.w);
+          wcost = fmaf(prm.w_coll * v, sgv.x, wcost);
+        }
+        if (parg >= 0 && (i == pi || i == pj)) {
+          const V3 xa = i == pi ? x : sphere_at(slot(r, t), pi);
+          const V3 xb = i == pj ? x : sphere_at(slot(r, t), pj);
+          const V3 d = xa - xb;
+          const float n = norm(d);
+          if (n > 0.f) {
+            const float f = prm.w_self / n;
+            gx = gx + (i == pi ? -f : f) * d;
+          }
+        }
+        if (gx.x != 0.f || gx.y != 0.f || gx.z != 0.f) {
+#pragma unroll
+          for (int j = 0; j < DMAX; ++j) {
+            if (j <= l) {
+              const float* T = LTt + j * 12;
+              const int ax = s_axis[j];
+              const V3 aj = v3(T[ax], T[4 + ax], T[8 + ax]);
+              const V3 rel = x - v3(T[3], T[7], T[11]);
+              acc[j] = fmaf(1.f, dot(gx, cross(aj, rel)), acc[j]);
+            }
+          }
+        }
+      }
+      // Eq. 14 pose cost at the last state
+      if (t == H && lane == 0) {
+        const float* T6 = LTt + (D - 1) * 12;
+        const float* Fe = s_fix + D * 12;
+        float E[12];
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr) {
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            float v = fmaf(T6[4 * rr], Fe[cc], fmaf(T6[4 * rr + 1], Fe[4 + cc], T6[4 * rr + 2] * Fe[8 + cc]));
+            E[4 * rr + cc] = cc == 3 ? v + T6[4 * rr + 3] : v;
+          }
+        }
+        const V3 e = v3(E[3] - s_prob.goal_p[0], E[7] - s_prob.goal_p[1], E[11] - s_prob.goal_p[2]);
+        const float rn = norm(e);
+        float tr = 0.f;
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+          for (int bb = 0; bb < 3; ++bb) tr = fmaf(s_prob.goal_R[aa * 3 + bb], E[aa * 4 + bb], tr);
+        const float dq = (3.f - tr) * 0.25f;
+        s_goal[r] = prm.w_goal_pos * logcoshf(prm.k_goal_pos * rn) +
+                    prm.w_goal_rot * logcoshf(prm.k_goal_rot * dq);
+        const float fp = rn > 1e-30f
+                             ? prm.w_goal_pos * prm.k_goal_pos * tanhf(prm.k_goal_pos * rn) / rn
+                             : prm.w_goal_pos * prm.k_goal_pos * prm.k_goal_pos;
+        const V3 dp = fp * e;
+        const float fr = -0.25f * prm.w_goal_rot * prm.k_goal_rot * tanhf(prm.k_goal_rot * dq);
+        // sum over columns c of R_c x dR_c, dR = fr R_g
+        V3 w = v3(0.f, 0.f, 0.f);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          const V3 Rc = v3(E[cc], E[4 + cc], E[8 + cc]);
+          const V3 Gc = fr * v3(s_prob.goal_R[cc], s_prob.goal_R[3 + cc], s_prob.goal_R[6 + cc]);
+          w = w + cross(Rc, Gc);
+        }
+        const V3 pe = v3(E[3], E[7], E[11]);
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) {
+          if (j < D) {
+            const float* T = LTt + j * 12;
+            const int ax = s_axis[j];
+            const V3 aj = v3(T[ax], T[4 + ax], T[8 + ax]);
+            const V3 rel = pe - v3(T[3], T[7], T[11]);
+            acc[j] += dot(dp, cross(aj, rel)) + dot(aj, w);
+          }
+        }
+      }
+      wcost = warp_sum(wcost);
+#pragma unroll
+      for (int j = 0; j < DMAX; ++j) acc[j] = warp_sum(acc[j]);
+      if (lane == 0) {
+        s_stw[sg] = wcost;
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j)
+          if (j < D) s_gth[sg * D + j] = acc[j];
+      }
+    }
+
+    // ---- Eq. 17 position bound; App. A.5 stencils with Eq. 16 and Eq. 17 on v, a, j
+    const int NS = H + 1;
+    for (int k = tid; k < S * D; k += nthr) {
+      const int j = k % D;
+      float sl;
+      s_pb[k] = prm.w_bound * bound_cost(s_th[k], s_lim[j], s_lim[D + j], e2, inv_e2, sl);
+    }
+    // padded sequence of App. A.2: 3 copies of q_start, theta_1..theta_H, 2 copies of theta_H
+    auto ext = [&](int r, int n, int j) -> float {
+      if (n <= 2) return s_prob.q_start[j];
+      if (n >= H + 2) return s_th[(r * H + H - 1) * D + j];
+      return s_th[(r * H + n - 3) * D + j];
+    };
+    const float inv12dt = 1.f / (12.f * dt), inv12dt2 = 1.f / (12.f * dt * dt),
+                inv2dt3 = 1.f / (2.f * dt * dt * dt);
+    if (!ik) {
+      for (int k = tid; k < nt * NS * D; k += nthr) {
+        const int r = k / (NS * D), rem = k % (NS * D), e = rem / D + 2, j = rem % D;
+        const float qm2 = ext(r, e - 2, j), qm1 = ext(r, e - 1, j), q0 = ext(r, e, j),
+                    qp1 = ext(r, e + 1, j), qp2 = ext(r, e + 2, j);
+        const float vel = (qm2 - 8.f * qm1 + 8.f * qp1 - qp2) * inv12dt;
+        const float accl = (-qm2 + 16.f * qm1 - 30.f * q0 + 16.f * qp1 - qp2) * inv12dt2;
+        const float jrk = (-qm2 + 2.f * qm1 - 2.f * qp1 + qp2) * inv2dt3;
+        float sm = prm.w_acc * accl * accl + prm.w_jerk * jrk * jrk;
+        float dv = 0.f, da = 2.f * prm.w_acc * accl, dj = 2.f * prm.w_jerk * jrk;
+        if (flags & CR_VEL_COST) {
+          sm += prm.w_vel * logcoshf(prm.k_vel * vel);
+          dv += prm.w_vel * prm.k_vel * tanhf(prm.k_vel * vel);
+        }
+        float s1, s2, s3;
+        const float vm = s_lim[2 * D + j], am = s_lim[3 * D + j], jm = s_lim[4 * D + j];
+        const float db = bound_cost(vel, -vm, vm, e2, inv_e2, s1) +
+                         bound_cost(accl, -am, am, e2, inv_e2, s2) +
+                         bound_cost(jrk, -jm, jm, e2, inv_e2, s3);
+        dv += prm.w_bound * s1;
+        da += prm.w_bound * s2;
+        dj += prm.w_bound * s3;
+        s_sten[3 * k] = dv;
+        s_sten[3 * k + 1] = da;
+        s_sten[3 * k + 2] = dj;
+        s_sm[k] = sm;
+        s_db[k] = prm.w_bound * db;
+      }
+    }
+    __syncthreads();
+
+    // ---- gradient: kinematic part + position bound + stencil transpose
+    for (int k = tid; k < S * D; k += nthr) {
+      const int sg = k / D, j = k % D, r = sg / H, t = sg % H + 1;
+      float sl;
+      bound_cost(s_th[k], s_lim[j], s_lim[D + j], e2, inv_e2, sl);
+      float g = s_gth[k] + prm.w_bound * sl;
+      if (!ik) {
+        const int nhi = t == H ? H + 4 : t + 2;
+        for (int n = t + 2; n <= nhi; ++n) {
+          const int elo = max(2, n - 2), ehi = min(H + 2, n + 2);
+          for (int e = elo; e <= ehi; ++e) {
+            const int o = n - e;  // position of theta in the stencil of sample e
+            const float* sd = s_sten + 3 * ((r * NS + e - 2) * D + j);
+            const float cv = o == -2 ? 1.f : o == -1 ? -8.f : o == 0 ? 0.f : o == 1 ? 8.f : -1.f;
+            const float ca = o == -2 ? -1.f : o == -1 ? 16.f : o == 0 ? -30.f : o == 1 ? 16.f : -1.f;
+            const float cj = o == -2 ? -1.f : o == -1 ? 2.f : o == 0 ? 0.f : o == 1 ? -2.f : 1.f;
+            g += sd[0] * cv * inv12dt + sd[1] * ca * inv12dt2 + sd[2] * cj * inv2dt3;
+          }
+        }
+      }
+      if (a.grad) a.grad[vbase + k] = g;
+    }
+
+    // ---- per-trajectory cost in a fixed order
+    for (int r = warp; r < nt; r += nw) {
+      float tw = 0.f, ts = 0.f, tb = 0.f, tsm = 0.f;
+      for (int t = lane; t < H; t += 32) {
+        tw += s_stw[r * H + t];
+        if (selfc) ts += prm.w_self * s_sts[r * H + t];
+      }
+      for (int k = lane; k < H * D; k += 32) tb += s_pb[r * H * D + k];
+      if (!ik) {
+        for (int k = lane; k < NS * D; k += 32) {
+          tb += s_db[r * NS * D + k];
+          tsm += s_sm[r * NS * D + k];
+        }
+      }
+      tw = warp_sum(tw);
+      ts = warp_sum(ts);
+      tb = warp_sum(tb);
+      tsm = warp_sum(tsm);
+      if (lane == 0) {
+        const int gi = s_prob.traj_base + r0 + r;
+        const float tg = s_goal[r];
+        a.cost[gi] = tw + ts + tb + tsm + tg;
+        if (a.cfree) a.cfree[gi] = (uint8_t)(s_free[r] != 0);
+        if (a.terms) {
+          float* tt = a.terms + (long long)gi * CR_N_TERMS;
+          tt[0] = tw;
+          tt[1] = ts;
+          tt[2] = tb;
+          tt[3] = tsm;
+          tt[4] = tg;
+        }
+      }
+    }
+  }
+}
+
+// Forward kinematics of N configurations, one thread each.
+__global__ void k_fk(RobotView rb, const float* __restrict__ theta, int n, float* spheres, float* ee,
+                     float* link_tf) {
+  __shared__ float s_fix[(kMaxDof + 1) * 12];
+  __shared__ int s_axis[kMaxDof];
+  const int D = rb.dof;
+  for (int k = threadIdx.x; k < (D + 1) * 12; k += blockDim.x) s_fix[k] = rb.fixed_tf[k];
+  for (int k = threadIdx.x; k < D; k += blockDim.x) s_axis[k] = rb.axis[k];
+  __syncthreads();
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  float q[kMaxDof];
+  for (int j = 0; j < D; ++j) q[j] = theta[(long long)b * D + j];
+  float LT[kMaxDof * 12];
+  fk_chain(s_fix, s_axis, D, q, LT);
+  if (link_tf)
+    for (int k = 0; k < D * 12; ++k) link_tf[(long long)b * D * 12 + k] = LT[k];
+  if (ee) {
+    const float* T6 = LT + (D - 1) * 12;
+    const float* Fe = s_fix + D * 12;
+    for (int rr = 0; rr < 3; ++rr)
+      for (int cc = 0; cc < 4; ++cc) {
+        float v = fmaf(T6[4 * rr], Fe[cc], fmaf(T6[4 * rr + 1], Fe[4 + cc], T6[4 * rr + 2] * Fe[8 + cc]));
+        ee[(long long)b * 12 + 4 * rr + cc] = cc == 3 ? v + T6[4 * rr + 3] : v;
+      }
+  }
+  if (spheres) {
+    for (int i = 0; i < rb.n_spheres; ++i) {
+      const float4 c = rb.spheres[i];
+      const V3 x = tf_point(LT + rb.sphere_link[i] * 12, c.x, c.y, c.z);
+      reinterpret_cast<float4*>(spheres)[(long long)b * rb.n_spheres + i] = make_float4(x.x, x.y, x.z, c.w);
+    }
+  }
+}
+
+}  // namespace
+
+int eval_smem_bytes(const EvalArgs& a, int block) {
+  EvalSmem L;
+  L.build(a.rb.dof, a.rb.n_spheres, a.rb.n_pairs, a.max_traj, a.max_states, a.max_horizon,
+          block / 32);
+  return L.bytes;
+}
+
+cudaError_t launch_eval(const EvalArgs& a, int grid, int block, cudaStream_t stream) {
+  const int smem = eval_smem_bytes(a, block);
+  if (a.rb.dof <= 8) {
+    cudaError_t e = cudaFuncSetAttribute(k_eval<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_eval<8><<<grid, block, smem, stream>>>(a);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_eval<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_eval<16><<<grid, block, smem, stream>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fk(const RobotView& rb, const float* theta, int n, float* spheres, float* ee,
+                      float* link_tf, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int block = 128;
+  k_fk<<<(n + block - 1) / block, block, 0, stream>>>(rb, theta, n, spheres, ee, link_tf);
+  return cudaGetLastError();
+}
+
+}  // namespace crgb

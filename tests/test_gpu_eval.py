@@ -1,0 +1,250 @@
+"""GPU parity of forward kinematics and of the fused cost-and-gradient kernel
+against the FP64 oracle, through the C ABI.
+
+Tolerances (FP32 GPU vs FP64 oracle on the same float32-rounded inputs):
+  sphere centres |d| <= 1e-5 m; costs |d| <= 1e-4 max(|ref|, 1e-2) per term and
+  total; gradient per trajectory ||d|| <= 1e-3 ||ref|| + 1e-6; collision-free
+  flags bit-exact.  A trajectory whose oracle evaluation took a discrete
+  decision (sweep stop, collision test, face or pair argmax, clearance sign)
+  within 1e-5 m of its threshold may differ: FP32 rounding can flip such a
+  decision.  Those trajectories are counted and must stay a minority.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2310_17274_gb300 import crgb, synth
+
+from scenes import f32, line_search_batch, scene
+
+pytestmark = pytest.mark.gpu
+
+NEAR = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2310_17274_gb300 import build
+    build.build_library()
+    oracle.build()
+    assert torch.cuda.is_available()
+
+
+def _gpu_eval(rb, w, pr, theta, params=None):
+    R = crgb.Robot(rb)
+    W = crgb.World(w)
+    spec = crgb.ProblemSpec(W, pr.q_start, pr.goal, theta.shape[1])
+    out = crgb.evaluate(R, spec, torch.tensor(theta, dtype=torch.float32, device="cuda"), params)
+    torch.cuda.synchronize()
+    return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+
+
+def compare(gpu, ref, max_near_frac=0.5, label=""):
+    """Apply the parity bar; returns (n_compared, n_near)."""
+    near = ref["margin"] < NEAR
+    B = len(ref["cost"])
+    assert near.mean() <= max_near_frac, f"{label}: too many near-threshold trajectories ({near.sum()}/{B})"
+    for b in range(B):
+        if near[b]:
+            continue
+        tol = 1e-4 * np.maximum(np.abs(ref["terms"][b]), 1e-2)
+        assert np.all(np.abs(gpu["terms"][b] - ref["terms"][b]) <= tol), \
+            (label, b, gpu["terms"][b], ref["terms"][b])
+        assert abs(gpu["cost"][b] - ref["cost"][b]) <= 1e-4 * max(abs(ref["cost"][b]), 1e-2), \
+            (label, b, gpu["cost"][b], ref["cost"][b])
+        if gpu.get("grad") is not None and ref.get("grad") is not None:
+            err = np.linalg.norm(gpu["grad"][b] - ref["grad"][b])
+            assert err <= 1e-3 * np.linalg.norm(ref["grad"][b]) + 1e-6, \
+                (label, b, err, np.linalg.norm(ref["grad"][b]))
+        assert bool(gpu["cfree"][b]) == bool(ref["cfree"][b]), (label, b)
+    return B - int(near.sum()), int(near.sum())
+
+
+# ---------------------------------------------------------------------------
+# forward kinematics
+# ---------------------------------------------------------------------------
+
+def test_fk_parity():
+    rb, _, _ = scene(spheres=synth.SPHERES_60)
+    rng = np.random.default_rng(0)
+    q = f32(synth.uniform_config(rng, rb, 300))
+    R = crgb.Robot(rb)
+    sp, ee, lt = crgb.fk(R, torch.tensor(q, dtype=torch.float32, device="cuda"), link_tf=True)
+    sp, ee, lt = sp.cpu().numpy(), ee.cpu().numpy(), lt.cpu().numpy()
+    for n in range(len(q)):
+        lt_r, sp_r, ee_r = oracle.fk(rb, q[n])
+        assert np.abs(sp[n, :, :3] - sp_r[:, :3]).max() <= 1e-5
+        assert np.array_equal(sp[n, :, 3], sp_r[:, 3].astype(np.float32))
+        assert np.abs(ee[n] - ee_r).max() <= 1e-5
+        assert np.abs(lt[n] - lt_r).max() <= 1e-5
+
+
+def test_fk_empty_and_single():
+    rb, _, _ = scene()
+    R = crgb.Robot(rb)
+    sp, ee, _ = crgb.fk(R, torch.zeros((0, rb.dof), device="cuda"))
+    assert sp.shape[0] == 0
+    sp, ee, _ = crgb.fk(R, torch.zeros((1, rb.dof), device="cuda"))
+    _, sp_r, ee_r = oracle.fk(rb, np.zeros(rb.dof))
+    assert np.abs(sp.cpu().numpy()[0, :, :3] - sp_r[:, :3]).max() <= 1e-6
+
+
+# ---------------------------------------------------------------------------
+# fused evaluation
+# ---------------------------------------------------------------------------
+
+def test_eval_parity_tiny():
+    """Tiny workload: 7-DOF, 42 spheres, 8 boxes, 4 seeds x 4 step sizes x 32 steps."""
+    rb, w, pr = scene()
+    theta = line_search_batch(pr, np.random.default_rng(1))
+    gpu = _gpu_eval(rb, w, pr, theta)
+    ref = oracle.evaluate(rb, w, pr.q_start, pr.goal, theta)
+    assert np.any(ref["terms"][:, 0] > 0), "world term inactive: scene too easy"
+    n_cmp, _ = compare(gpu, ref, label="tiny")
+    assert n_cmp >= 8
+
+
+@pytest.mark.parametrize("flags", [
+    crgb.SPEED | crgb.SELF,                      # sweep off
+    crgb.SWEPT | crgb.SELF,                      # speed off
+    crgb.SWEPT | crgb.SPEED,                     # self off
+    crgb.SWEPT | crgb.SPEED | crgb.SELF | crgb.VEL_COST,
+])
+def test_eval_parity_flags(flags):
+    rb, w, pr = scene(n_boxes=12, world_seed=3, problem_seed=4)
+    theta = line_search_batch(pr, np.random.default_rng(2))
+    p = dict(flags=flags | crgb.WOLFE)
+    gpu = _gpu_eval(rb, w, pr, theta, p)
+    ref = oracle.evaluate(rb, w, pr.q_start, pr.goal, theta, p)
+    compare(gpu, ref, label=f"flags={flags}")
+
+
+def test_eval_parity_trajopt_shape():
+    """Trajectory-optimisation shape: 60 spheres, 32 boxes, H = 48 (8 trajectories)."""
+    rb, w, pr = scene(spheres=synth.SPHERES_60, n_boxes=32, n_seeds=4, horizon=48, world_seed=2,
+                      problem_seed=11)
+    theta = line_search_batch(pr, np.random.default_rng(3), alphas=(0.1, 0.5))
+    gpu = _gpu_eval(rb, w, pr, theta, dict(alpha=list(synth.ALPHA_8)))
+    ref = oracle.evaluate(rb, w, pr.q_start, pr.goal, theta)
+    compare(gpu, ref, max_near_frac=0.9, label="trajopt")
+
+
+def test_eval_parity_ik():
+    """IK shape: H = 1, IK mode, 60 spheres, 40 boxes, a ragged batch of 50."""
+    rb, w, _ = scene(spheres=synth.SPHERES_60, n_boxes=40, world_seed=3)
+    rng = np.random.default_rng(5)
+    qg = synth.uniform_config(rng, rb)
+    goal = f32(oracle.goal_pose_from_fk(rb, qg))
+    theta = f32(synth.uniform_config(rng, rb, 50)[:, None, :])
+    pr = synth.Problem(world=w, q_start=f32(synth.uniform_config(rng, rb)), goal=goal, seeds=theta)
+    p = dict(flags=crgb.IK_MODE | crgb.SELF)
+    gpu = _gpu_eval(rb, w, pr, theta, p)
+    ref = oracle.evaluate(rb, w, pr.q_start, pr.goal, theta, p)
+    n_cmp, _ = compare(gpu, ref, label="ik")
+    assert n_cmp >= 40
+    assert gpu["cfree"].any() and not gpu["cfree"].all()
+
+
+def test_eval_many_boxes_and_max_horizon():
+    """More boxes than one shared-memory chunk (150 > 64) and the largest horizon."""
+    rb, w, pr = scene(n_boxes=150, n_seeds=2, horizon=128, world_seed=8, problem_seed=3)
+    gpu = _gpu_eval(rb, w, pr, pr.seeds)
+    ref = oracle.evaluate(rb, w, pr.q_start, pr.goal, pr.seeds)
+    compare(gpu, ref, max_near_frac=1.0, label="K=150,H=128")
+
+
+def test_eval_edge_cases():
+    rb, w, pr = scene(n_seeds=3, horizon=5)
+    # no boxes
+    w0 = synth.World(pose=np.zeros((0, 7)), half_ext=np.zeros((0, 3)))
+    gpu = _gpu_eval(rb, w0, pr, pr.seeds)
+    ref = oracle.evaluate(rb, w0, pr.q_start, pr.goal, pr.seeds)
+    compare(gpu, ref, max_near_frac=1.0, label="K=0")
+    assert np.all(gpu["terms"][:, 0] == 0)
+    # H = 1 outside IK mode (stencil over one state) and H = 2
+    for H in (1, 2):
+        th = pr.seeds[:, :H].copy()
+        gpu = _gpu_eval(rb, w, pr, th)
+        ref = oracle.evaluate(rb, w, pr.q_start, pr.goal, th)
+        compare(gpu, ref, max_near_frac=1.0, label=f"H={H}")
+    # disabled spheres (negative radius)
+    rb2 = synth.Robot(**{**rb.__dict__, "spheres": rb.spheres.copy()})
+    rb2.spheres[::3, 3] = -1.0
+    gpu = _gpu_eval(rb2, w, pr, pr.seeds)
+    ref = oracle.evaluate(rb2, w, pr.q_start, pr.goal, pr.seeds)
+    compare(gpu, ref, max_near_frac=1.0, label="disabled spheres")
+    # empty batch is a no-op
+    R, W = crgb.Robot(rb), crgb.World(w)
+    spec = crgb.ProblemSpec(W, pr.q_start, pr.goal, 5)
+    out = crgb.evaluate(R, spec, torch.zeros((0, 5, rb.dof), device="cuda"))
+    assert out["cost"].numel() == 0
+
+
+def test_eval_rejects_bad_sizes():
+    rb, w, pr = scene()
+    R, W = crgb.Robot(rb), crgb.World(w)
+    spec = crgb.ProblemSpec(W, pr.q_start, pr.goal, 129)
+    with pytest.raises(crgb.CrError, match="horizon"):
+        crgb.evaluate(R, spec, torch.zeros((1, 129, rb.dof), device="cuda"))
+    spec = crgb.ProblemSpec(W, pr.q_start, pr.goal, 4)
+    with pytest.raises(crgb.CrError, match="history"):
+        crgb.evaluate(R, spec, torch.zeros((1, 4, rb.dof), device="cuda"), dict(history=0))
+
+
+def test_eval_deterministic_and_batch_independent():
+    """Same inputs give bit-identical outputs, and a trajectory's result does
+    not depend on what else is in the batch."""
+    rb, w, pr = scene(spheres=synth.SPHERES_60, n_boxes=32, n_seeds=8, horizon=48, world_seed=2)
+    theta = line_search_batch(pr, np.random.default_rng(7))
+    a = _gpu_eval(rb, w, pr, theta)
+    b = _gpu_eval(rb, w, pr, theta)
+    for k in ("cost", "grad", "cfree", "terms"):
+        assert np.array_equal(a[k], b[k]), k
+    sub = _gpu_eval(rb, w, pr, theta[5:9])
+    for k in ("cost", "grad", "cfree", "terms"):
+        assert np.array_equal(a[k][5:9], sub[k]), k
+
+
+def test_eval_full_size_sampled():
+    """Bench configuration (60 spheres, 32 boxes, 32 seeds x 8 step sizes x 48
+    steps in one launch): sampled trajectories against the oracle, and
+    cost = sum of terms everywhere."""
+    rb, w, pr = scene(spheres=synth.SPHERES_60, n_boxes=32, n_seeds=32, horizon=48,
+                      world_seed=2, problem_seed=2)
+    theta = line_search_batch(pr, np.random.default_rng(9), alphas=synth.ALPHA_8)
+    assert theta.shape == (256, 48, 7)
+    gpu = _gpu_eval(rb, w, pr, theta)
+    np.testing.assert_allclose(gpu["cost"], gpu["terms"].sum(1), rtol=1e-5)
+    idx = np.random.default_rng(0).choice(256, 10, replace=False)
+    ref = oracle.evaluate(rb, w, pr.q_start, pr.goal, theta[idx])
+    compare({k: v[idx] for k, v in gpu.items()}, ref, max_near_frac=0.9, label="full-size sample")
+
+
+def test_autograd_matches_oracle_finite_differences():
+    """Gradient through torch.autograd.Function equals central finite
+    differences (h = 1e-4, FP64) of the oracle's cost (sweep off: its
+    gradient is a surrogate by design)."""
+    from paper_2310_17274_gb300.autograd import trajectory_cost
+    rb, w, pr = scene(n_boxes=10, n_seeds=2, horizon=8, world_seed=5, problem_seed=5)
+    p = dict(flags=crgb.SPEED | crgb.SELF | crgb.WOLFE)
+    R, W = crgb.Robot(rb), crgb.World(w)
+    spec = crgb.ProblemSpec(W, pr.q_start, pr.goal, 8)
+    th = torch.tensor(pr.seeds, dtype=torch.float32, device="cuda", requires_grad=True)
+    cost = trajectory_cost(th, R, spec, crgb.make_params(p))
+    (cost * torch.tensor([1.0, 2.0], device="cuda")).sum().backward()
+    g = th.grad.cpu().numpy()
+    h = 1e-4
+    num = np.zeros_like(pr.seeds)
+    for b in range(2):
+        for t in range(8):
+            for j in range(rb.dof):
+                tp, tm = pr.seeds[b:b + 1].copy(), pr.seeds[b:b + 1].copy()
+                tp[0, t, j] += h
+                tm[0, t, j] -= h
+                cp = oracle.evaluate(rb, w, pr.q_start, pr.goal, tp, p, want_grad=False)["cost"][0]
+                cm = oracle.evaluate(rb, w, pr.q_start, pr.goal, tm, p, want_grad=False)["cost"][0]
+                num[b, t, j] = (cp - cm) / (2 * h) * (1.0 + b)
+    for b in range(2):
+        err = np.linalg.norm(g[b] - num[b])
+        assert err <= 1e-3 * np.linalg.norm(num[b]) + 1e-6, (b, err, np.linalg.norm(num[b]))
