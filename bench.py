@@ -1,0 +1,531 @@
+#!/usr/bin/env python
+"""Benchmark: seed x timestep cost+grad evaluations per second of the
+trajectory-optimisation workload (7-DOF chain, 60 spheres, 32 boxes, 32 seeds
+x 48 timesteps, 8 line-search step sizes, 100 L-BFGS iterations), one step =
+one whole solve of that problem through the graph-captured batched path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): independent replicas,
+one problem per rank, max-over-ranks timing, value = total evaluations / time.
+--impl reference times the FP64 CPU oracle (single-threaded) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "seed·timestep cost+grad evals/s"
+UNIT = "evals/s"
+WORKLOAD = ("trajopt: 7-DOF revolute chain, 60 spheres, 32 cuboids, 32 seeds x 48 timesteps, "
+            "8 line-search step sizes, 100 L-BFGS iterations (history 6), FP32")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# workload (synthetic, seeded)
+# ---------------------------------------------------------------------------
+
+def make_workload(crgb, synth, seed_offset=0):
+    """Trajectory-optimisation problem; goal and box rejection through the
+    library's own kinematics / evaluation (no oracle on this path)."""
+    import torch
+    cfg = synth.CONFIGS["trajopt"]
+    rb = synth.make_robot(cfg.spheres_per_link, seed=0)
+    R = crgb.Robot(rb)
+    rng = np.random.default_rng(2 + seed_offset)
+    qs = synth.uniform_config(rng, rb)
+
+    def goal_fn(q):
+        _, ee, _ = crgb.fk(R, torch.tensor(q, dtype=torch.float32, device="cuda")[None], spheres=False)
+        E = ee[0].cpu().numpy().astype(np.float64).reshape(3, 4)
+        return np.concatenate([E[:, 3], _rot_to_quat(E[:, :3])])
+
+    ik_params = crgb.make_params(dict(flags=crgb.IK_MODE | crgb.SELF))
+
+    def reject(pose, he):
+        W1 = crgb.World(synth.World(pose=pose[None], half_ext=he[None]))
+        spec = crgb.ProblemSpec(W1, qs, np.array([0, 0, 0, 1.0, 0, 0, 0]), 1)
+        out = crgb.evaluate(R, spec, torch.tensor(qs, dtype=torch.float32, device="cuda").view(1, 1, -1),
+                            ik_params, want_grad=False, want_terms=False)
+        return not bool(out["cfree"][0])
+
+    world = synth.make_world(cfg.n_boxes, cfg.world_seed + seed_offset, reject)
+    pr = synth.make_problem(rb, world, 2 + seed_offset, cfg.n_seeds, cfg.horizon, goal_fn, q_start=qs)
+    return cfg, rb, R, world, pr
+
+
+def _rot_to_quat(R):
+    tr = np.trace(R)
+    if tr > 0:
+        s = np.sqrt(tr + 1.0) * 2
+        q = [0.25 * s, (R[2, 1] - R[1, 2]) / s, (R[0, 2] - R[2, 0]) / s, (R[1, 0] - R[0, 1]) / s]
+    elif R[0, 0] > R[1, 1] and R[0, 0] > R[2, 2]:
+        s = np.sqrt(1.0 + R[0, 0] - R[1, 1] - R[2, 2]) * 2
+        q = [(R[2, 1] - R[1, 2]) / s, 0.25 * s, (R[0, 1] + R[1, 0]) / s, (R[0, 2] + R[2, 0]) / s]
+    elif R[1, 1] > R[2, 2]:
+        s = np.sqrt(1.0 + R[1, 1] - R[0, 0] - R[2, 2]) * 2
+        q = [(R[0, 2] - R[2, 0]) / s, (R[0, 1] + R[1, 0]) / s, 0.25 * s, (R[1, 2] + R[2, 1]) / s]
+    else:
+        s = np.sqrt(1.0 + R[2, 2] - R[0, 0] - R[1, 1]) * 2
+        q = [(R[1, 0] - R[0, 1]) / s, (R[0, 2] + R[2, 0]) / s, (R[1, 2] + R[2, 1]) / s, 0.25 * s]
+    q = np.asarray(q)
+    return q / np.linalg.norm(q)
+
+
+def flop_per_state(dof, M, K, P):
+    """Algorithmic FP32 work of one state's cost + gradient (FMA = 2 FLOP):
+    kinematics 81/joint, sphere transform 18/sphere, box distance 35 per
+    (sphere, box), pair distance 12 per pair, Jacobian-transpose 17 per
+    (sphere, joint on its chain) with (dof+1)/2 joints on average, neighbour
+    spheres for the sweep and the speed metric 50/sphere, stencils and bounds
+    40/joint."""
+    return 81 * dof + 18 * M + 35 * M * K + 12 * P + 17 * M * (dof + 1) / 2 + 50 * M + 40 * dof
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = f"/tmp/crgb_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [l.split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for k, n in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2310_17274_gb300 import synth
+    oracle.build()
+    cfg = synth.CONFIGS["trajopt"]
+    rb = synth.make_robot(cfg.spheres_per_link, seed=0)
+    rng = np.random.default_rng(2)
+    qs = synth.uniform_config(rng, rb)
+    world = synth.make_world(cfg.n_boxes, cfg.world_seed,
+                             lambda p, h: oracle.start_collides_with_box(rb, qs, p, h))
+    pr = synth.make_problem(rb, world, 2, cfg.n_seeds, cfg.horizon,
+                            lambda q: oracle.goal_pose_from_fk(rb, q), q_start=qs)
+    # one step: cost + gradient of 8 seeds' trajectories (8 x 48 states), a
+    # bounded sample of one line-search batch (32 seeds x 8 step sizes)
+    sample = pr.seeds[:8]
+    states = sample.shape[0] * sample.shape[1]
+    for _ in range(args.warmup):
+        oracle.evaluate(rb, world, qs, pr.goal, sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.evaluate(rb, world, qs, pr.goal, sample)
+    dt = time.perf_counter() - t0
+    value = states * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"cost+grad of 8 seeds x 48 timesteps per step ({states} states)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(seconds=10.0):
+    """The oracle as it stands, single-threaded, on a bounded sample."""
+    import oracle
+    from paper_2310_17274_gb300 import synth
+    oracle.build()
+    cfg = synth.CONFIGS["trajopt"]
+    rb = synth.make_robot(cfg.spheres_per_link, seed=0)
+    rng = np.random.default_rng(2)
+    qs = synth.uniform_config(rng, rb)
+    world = synth.make_world(cfg.n_boxes, cfg.world_seed,
+                             lambda p, h: oracle.start_collides_with_box(rb, qs, p, h))
+    pr = synth.make_problem(rb, world, 2, cfg.n_seeds, cfg.horizon,
+                            lambda q: oracle.goal_pose_from_fk(rb, q), q_start=qs)
+    sample = pr.seeds[:8]
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        oracle.evaluate(rb, world, qs, pr.goal, sample)
+        n += 1
+    dt = time.perf_counter() - t0
+    states = sample.shape[0] * sample.shape[1] * n
+    return {"value": states / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} x cost+grad of 8 seeds x 48 timesteps ({states} states, {dt:.1f} s)"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="crgb")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extras", default="ik,uneven,plain")
+    ap.add_argument("--profile", type=int, default=0,
+                    help="only run N fused evaluations of one line-search batch inside the NVTX "
+                         "range crgb_eval (for ncu), then exit")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2310_17274_gb300 import build, crgb, synth
+    if rank == 0 or not os.path.exists(crgb.LIB_PATH):
+        build.build_library()
+    if ws > 1:
+        dist.barrier()
+
+    cfg, rb, R, world, pr = make_workload(crgb, synth, seed_offset=rank)
+    W = crgb.World(world)
+    B, H, D = pr.seeds.shape
+    P = crgb.make_params(dict(alpha=list(cfg.alphas)))
+    na = P.n_alpha
+    iters = cfg.iters
+    ctx = crgb.Context(local)
+    spec = crgb.ProblemSpec(W, pr.q_start, pr.goal, H, seeds=pr.seeds)
+    seeds_dev = torch.tensor(pr.seeds, dtype=torch.float32, device="cuda")
+    units = iters * B * na * H + B * H              # states evaluated per solve
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+
+    if args.profile:
+        cand = torch.tensor(np.repeat(pr.seeds, na, axis=0), dtype=torch.float32, device="cuda")
+        espec = crgb.ProblemSpec(W, pr.q_start, pr.goal, H)
+        crgb.evaluate(R, espec, cand, P)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("crgb_eval")
+        for _ in range(args.profile):
+            crgb.evaluate(R, espec, cand, P, want_terms=False)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "states_per_launch": int(cand.shape[0] * H)}))
+        return 0
+
+    def solve_dev(outs=None):
+        return crgb.solve(ctx, R, [spec], P, iters=iters, graph=True, persistent=True,
+                          device_seeds=[seeds_dev], outputs=outs)
+
+    outs = None
+    for _ in range(args.warmup):
+        outs = solve_dev(outs)
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps (inputs resident in HBM), L2 flushed between steps
+    times = []
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if ws > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("crgb_step")
+            ev0.record(stream)
+            outs = solve_dev(outs)
+            ev1.record(stream)
+            torch.cuda.nvtx.range_pop()
+            torch.cuda.synchronize()
+            times.append(ev0.elapsed_time(ev1) / 1e3)
+    clocks = clk.summary()
+    t_total = float(np.sum(times))
+    if ws > 1:
+        t = torch.tensor([t_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = units * args.steps * ws / t_total
+    launches_per_step = 2 + 2 * iters + 1
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    h_traj = torch.empty((B, H, D), dtype=torch.float32).pin_memory()
+    h_cost = torch.empty(B, dtype=torch.float32).pin_memory()
+    h_free = torch.empty(B, dtype=torch.uint8).pin_memory()
+    h_best = torch.empty(1, dtype=torch.int32).pin_memory()
+    e2e_times = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o = crgb.solve(ctx, R, [spec], P, iters=iters, graph=True, persistent=True, outputs=outs)[0]
+        h_traj.copy_(o.traj, non_blocking=True)
+        h_cost.copy_(o.cost, non_blocking=True)
+        h_free.copy_(o.cfree, non_blocking=True)
+        h_best.copy_(o.best, non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    t_e2e = float(np.sum(e2e_times))
+    if ws > 1:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = units * args.steps * ws / t_e2e
+    h2d = pr.seeds.size * 4
+    d2h = h_traj.numel() * 4 + h_cost.numel() * 4 + h_free.numel() + h_best.numel() * 4
+
+    # ---- dominant kernel: the fused evaluation of one line-search batch,
+    # timed alone with CUDA events on its stream
+    cand = torch.tensor(np.repeat(pr.seeds, na, axis=0), dtype=torch.float32, device="cuda")
+    espec = crgb.ProblemSpec(W, pr.q_start, pr.goal, H)
+    for _ in range(5):
+        crgb.evaluate(R, espec, cand, P)
+    n_ev = 50
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(n_ev):
+        crgb.evaluate(R, espec, cand, P, want_terms=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_eval = ev0.elapsed_time(ev1) / 1e3 / n_ev
+    fps = flop_per_state(D, rb.n_spheres, world.n, rb.n_pairs)
+    states_per_launch = B * na * H
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_tflops = n_sm * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 FMA lanes x 2 FLOP x clock
+    achieved = fps * states_per_launch / t_eval / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None, "kernel": "k_eval",
+                "launch_us": t_eval * 1e6, "states_per_launch": states_per_launch,
+                "flop_per_state": fps,
+                "peak_note": f"FP32 FMA peak: {n_sm} SMs x 128 lanes x 2 FLOP x {sm_max:.0f} MHz (derived)"}
+
+    extras = {}
+    want = set(args.extras.split(",")) if args.extras else set()
+    if rank == 0 and "plain" in want:
+        # plain per-problem GPU path: eager launches, no graph, grid-strided tiles
+        for _ in range(2):
+            crgb.solve(ctx, R, [spec], P, iters=iters, graph=False, persistent=False,
+                       device_seeds=[seeds_dev], outputs=outs)
+        torch.cuda.synchronize()
+        tp = []
+        for _ in range(5):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            crgb.solve(ctx, R, [spec], P, iters=iters, graph=False, persistent=False,
+                       device_seeds=[seeds_dev], outputs=outs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tp.append(e0.elapsed_time(e1) / 1e3)
+        extras["plain_gpu_path"] = {"value": units / float(np.mean(tp)), "unit": UNIT,
+                                    "ms_per_solve": float(np.mean(tp)) * 1e3,
+                                    "what": "same solve, eager launches, no CUDA graph"}
+    if rank == 0 and "ik" in want:
+        extras["ik"] = bench_ik(crgb, synth, ctx, R, rb)
+    if rank == 0 and "uneven" in want:
+        extras["uneven"] = bench_uneven(crgb, synth, ctx, R, rb)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "solve": "graph-captured, persistent evaluation",
+                           "units_per_step": units, "parallelism": f"replicas x{ws}",
+                           "l2": "flushed between steps (256 MB write)"},
+                "clocks": clocks,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h),
+                        "what": "cr_solve with host seeds, results read back to pinned host memory"},
+                "gpu_launches": launches_per_step * args.steps,
+                "roofline": roofline,
+                "cpu_baseline": cpu,
+                "extras": extras}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def bench_ik(crgb, synth, ctx, R, rb, n_goals=1000, n_seeds=32, iters=50):
+    """Batched collision-free IK: 1000 goals x 32 seeds (H = 1) in one solve;
+    solved = best seed collision-free, within 5 mm and d_q <= 1e-3."""
+    import torch
+    cfg = synth.CONFIGS["ik"]
+    rng = np.random.default_rng(3)
+    qs = synth.uniform_config(rng, rb)
+    ikp = crgb.make_params(dict(flags=crgb.IK_MODE | crgb.SELF | crgb.WOLFE, alpha=list(cfg.alphas)))
+
+    def reject(pose, he):
+        W1 = crgb.World(synth.World(pose=pose[None], half_ext=he[None]))
+        spec = crgb.ProblemSpec(W1, qs, np.array([0, 0, 0, 1.0, 0, 0, 0]), 1)
+        out = crgb.evaluate(R, spec, torch.tensor(qs, dtype=torch.float32, device="cuda").view(1, 1, -1),
+                            ikp, want_grad=False, want_terms=False)
+        return not bool(out["cfree"][0])
+
+    world = synth.make_world(cfg.n_boxes, cfg.world_seed, reject)
+    W = crgb.World(world)
+    qg = synth.uniform_config(rng, rb, n_goals)
+    _, ee, _ = crgb.fk(R, torch.tensor(qg, dtype=torch.float32, device="cuda"), spheres=False)
+    ee = ee.cpu().numpy().astype(np.float64).reshape(-1, 3, 4)
+    goals = np.stack([np.concatenate([e[:, 3], _rot_to_quat(e[:, :3])]) for e in ee])
+    seeds = synth.uniform_config(rng, rb, n_goals * n_seeds).reshape(n_goals, n_seeds, 1, rb.dof)
+    specs = [crgb.ProblemSpec(W, qs, goals[g], 1, seeds=seeds[g]) for g in range(n_goals)]
+    outs = None
+    for _ in range(3):
+        outs = crgb.solve(ctx, R, specs, ikp, iters=iters, graph=True, persistent=True, outputs=outs)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        outs = crgb.solve(ctx, R, specs, ikp, iters=iters, graph=True, persistent=True, outputs=outs)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    t = float(np.median(ts))
+    # success with the library's own kinematics
+    best = torch.stack([o.traj[int(o.best), 0] for o in outs])
+    free = np.array([bool(o.cfree[int(o.best)]) for o in outs])
+    _, eb, _ = crgb.fk(R, best.contiguous(), spheres=False)
+    eb = eb.cpu().numpy().astype(np.float64).reshape(-1, 3, 4)
+    pos_err = np.linalg.norm(eb[:, :, 3] - goals[:, :3], axis=1)
+    Rg = np.stack([_quat_rot(g[3:]) for g in goals])
+    dq = (3 - np.einsum("nij,nij->n", Rg, eb[:, :, :3])) / 4
+    solved = free & (pos_err <= 5e-3) & (dq <= 1e-3)
+    return {"goals": n_goals, "seeds": n_seeds, "iters": iters, "ms_per_batch": t * 1e3,
+            "ik_solves_per_s": n_goals / t, "success_rate": float(solved.mean()),
+            "evals_per_s": n_goals * n_seeds * (iters * ikp.n_alpha + 1) / t}
+
+
+def _quat_rot(q):
+    w, x, y, z = q / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def bench_uneven(crgb, synth, ctx, R, rb, iters=100):
+    """64 problems with uneven box counts, seeds and horizons in one
+    persistent graph-captured solve, against 64 separate plain solves."""
+    import torch
+    shapes = synth.uneven_shapes(4, 64)
+    rng = np.random.default_rng(4)
+    specs, worlds, units = [], [], 0
+    for k, (K, B, H) in enumerate(shapes):
+        world = synth.make_world(K, 400 + k)
+        W = crgb.World(world)
+        worlds.append(W)
+        qs = synth.uniform_config(rng, rb)
+        qg = synth.uniform_config(rng, rb)
+        seeds = synth.linear_seeds(rng, rb, qs, qg, B, H)
+        goal = np.array([0.3, 0.2, 0.5, 1, 0, 0, 0.0])
+        specs.append(crgb.ProblemSpec(W, qs, goal, H, seeds=seeds))
+        units += iters * B * 4 * H + B * H
+    P = crgb.make_params(None)
+    outs = None
+    for _ in range(2):
+        outs = crgb.solve(ctx, R, specs, P, iters=iters, graph=True, persistent=True, outputs=outs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        outs = crgb.solve(ctx, R, specs, P, iters=iters, graph=True, persistent=True, outputs=outs)
+    e1.record()
+    torch.cuda.synchronize()
+    t_batched = e0.elapsed_time(e1) / 1e3 / 3
+    # plain: 64 separate eager solves
+    single = [None] * len(specs)
+    for k, s in enumerate(specs):
+        single[k] = crgb.solve(ctx, R, [s], P, iters=iters, graph=False, persistent=False)
+    torch.cuda.synchronize()
+    e0.record()
+    for k, s in enumerate(specs):
+        crgb.solve(ctx, R, [s], P, iters=iters, graph=False, persistent=False, outputs=single[k])
+    e1.record()
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3
+    same = all(torch.equal(a.cost, b[0].cost) for a, b in zip(outs, single))
+    return {"problems": len(specs), "iters": iters, "evals_per_step": units,
+            "batched_ms": t_batched * 1e3, "batched_evals_per_s": units / t_batched,
+            "plain_ms": t_plain * 1e3, "plain_evals_per_s": units / t_plain,
+            "speedup": t_plain / t_batched, "results_identical": bool(same)}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

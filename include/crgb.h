@@ -212,6 +212,43 @@ cr_status cr_opt_propose(const cr_robot* robot, const cr_params* params, const c
 cr_status cr_opt_select(const cr_robot* robot, const cr_params* params, const cr_opt_state* st,
                         void* stream);
 
+/* ------------------------------------------------------------------------- */
+/* Runtime: context, batched solve                                            */
+/* ------------------------------------------------------------------------- */
+typedef struct cr_ctx cr_ctx;
+
+/* A context on CUDA device `device` owns the solver workspace (grown on
+ * demand, capped by mem_budget bytes; 0 = no cap), the captured CUDA graphs
+ * and the autotune table.  Not thread-safe: one host thread per context. */
+cr_status cr_context_create(int device, size_t mem_budget, cr_ctx** out);
+void cr_context_destroy(cr_ctx* ctx);
+
+/* Output of one problem: device buffers owned by the caller (any may be NULL). */
+typedef struct {
+  float* traj;     /* [B][H][dof] best iterate of every seed */
+  float* cost;     /* [B] its cost */
+  uint8_t* cfree;  /* [B] its collision-free flag */
+  int32_t* best;   /* [1] index of the lowest-cost collision-free seed, else of the lowest-cost seed */
+} cr_result;
+
+#define CR_SOLVE_GRAPH 1u       /* capture the whole solve as one CUDA graph, replayed on later calls */
+#define CR_SOLVE_PERSISTENT 2u  /* evaluation launches sized to the GPU, tiles taken from a device counter */
+#define CR_SOLVE_DEVICE_SEEDS 4u /* problems[p].seeds point to device memory instead of host memory */
+
+/* Solve n_problems problems (each with its own world, start, goal, seed
+ * count and horizon) together (Sec. 4.1): evaluate the seeds, then `iters`
+ * iterations of L-BFGS step -> parallel noisy line search over all
+ * candidates of all problems in one evaluation launch -> selection and
+ * best-iterate update, then the per-problem result.  Seeds are host memory
+ * (problems[p].seeds, [B][H][dof]; device memory with CR_SOLVE_DEVICE_SEEDS)
+ * and are copied on `stream`; results are written on `stream`.  A problem's
+ * results are identical whether it is solved alone or with others.  The call
+ * waits until the previous call's small table upload has left its pinned
+ * staging buffer before reusing it. */
+cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
+                   const cr_params* params, int32_t iters, uint32_t solve_flags,
+                   const cr_result* results, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -58,6 +58,13 @@ class Problem(C.Structure):
                 ("horizon", C.c_int32), ("seeds", _fp)]
 
 
+class Result(C.Structure):
+    _fields_ = [("traj", _vp), ("cost", _vp), ("cfree", _vp), ("best", _vp)]
+
+
+SOLVE_GRAPH, SOLVE_PERSISTENT, SOLVE_DEVICE_SEEDS = 1, 2, 4
+
+
 class OptState(C.Structure):
     _fields_ = [("n_seeds", C.c_int32), ("horizon", C.c_int32),
                 ("x", _vp), ("g", _vp), ("c", _vp), ("x_prev", _vp), ("g_prev", _vp),
@@ -80,6 +87,10 @@ SIGNATURES = {
                  _vp], C.c_int32),
     "cr_opt_propose": ([_vp, C.POINTER(Params), C.POINTER(OptState), _vp], C.c_int32),
     "cr_opt_select": ([_vp, C.POINTER(Params), C.POINTER(OptState), _vp], C.c_int32),
+    "cr_context_create": ([C.c_int, C.c_size_t, C.POINTER(_vp)], C.c_int32),
+    "cr_context_destroy": ([_vp], None),
+    "cr_solve": ([_vp, _vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), C.c_int32, C.c_uint32,
+                  C.POINTER(Result), _vp], C.c_int32),
 }
 
 
@@ -306,3 +317,63 @@ def opt_select(robot: Robot, params, st: OptBuffers, stream=None):
     s = st.struct()
     check(lib().cr_opt_select(robot.handle, C.byref(P), C.byref(s), _stream(stream)),
           "cr_opt_select")
+
+
+# ---------------------------------------------------------------------------
+# runtime
+# ---------------------------------------------------------------------------
+
+class Context:
+    """Solver context on one device (workspace, captured graphs, autotune table)."""
+
+    def __init__(self, device: int = 0, mem_budget: int = 0):
+        h = _vp()
+        check(lib().cr_context_create(int(device), int(mem_budget), C.byref(h)), "cr_context_create")
+        self.handle = h
+        self.device = device
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.cr_context_destroy(h)
+            self.handle = None
+
+
+class SolveOutput:
+    """Device result buffers of one problem (torch tensors)."""
+
+    def __init__(self, n_seeds, horizon, dof, device="cuda"):
+        import torch
+        self.traj = torch.empty((n_seeds, horizon, dof), device=device)
+        self.cost = torch.empty(n_seeds, device=device)
+        self.cfree = torch.empty(n_seeds, device=device, dtype=torch.uint8)
+        self.best = torch.empty(1, device=device, dtype=torch.int32)
+
+    def struct(self) -> Result:
+        return Result(_dptr(self.traj), _dptr(self.cost), _dptr(self.cfree), _dptr(self.best))
+
+
+def solve(ctx: Context, robot: Robot, problems, params=None, iters=25, graph=True,
+          persistent=True, outputs=None, stream=None, device_seeds=None):
+    """Optimise a batch of problems (ProblemSpec with host seeds) together.
+    With device_seeds (one CUDA tensor [B, H, dof] per problem) the seeds are
+    read from device memory instead.  Returns one SolveOutput per problem
+    (device tensors, valid once the stream has finished)."""
+    probs = list(problems)
+    n = len(probs)
+    structs = [p.struct() for p in probs]
+    if device_seeds is not None:
+        for s, t in zip(structs, device_seeds):
+            s.seeds = C.cast(C.c_void_p(t.data_ptr()), _fp)
+            s.n_seeds = int(t.shape[0])
+    arr = (Problem * n)(*structs)
+    if outputs is None:
+        outputs = [SolveOutput(s.n_seeds, p.horizon, robot.dof) for s, p in zip(structs, probs)]
+    res = (Result * n)(*[o.struct() for o in outputs])
+    P = params if isinstance(params, Params) else make_params(params)
+    flags = (SOLVE_GRAPH if graph else 0) | (SOLVE_PERSISTENT if persistent else 0)
+    if device_seeds is not None:
+        flags |= SOLVE_DEVICE_SEEDS
+    check(lib().cr_solve(ctx.handle, robot.handle, n, arr, C.byref(P), int(iters), flags, res,
+                         _stream(stream)), "cr_solve")
+    return outputs

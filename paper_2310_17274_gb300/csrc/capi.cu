@@ -38,17 +38,10 @@ cr_status cuda_fail(cudaError_t e, const char* what) {
 
 }  // namespace
 
-struct cr_robot {
-  int dof = 0, n_spheres = 0, n_pairs = 0;
-  void* dev = nullptr;
-  RobotView view{};
-  std::vector<float> q_lo, q_hi;
-};
-
-struct cr_world {
-  int n = 0;
-  BoxRows* dev = nullptr;
-};
+cr_status crgb::set_error(cr_status code, const char* msg) {
+  g_err = msg;
+  return code;
+}
 
 extern "C" {
 
@@ -154,8 +147,10 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
   r->view.axis = reinterpret_cast<const int*>(b + o_axis);
   r->view.sphere_link = reinterpret_cast<const int*>(b + o_link);
   r->view.pairs = reinterpret_cast<const uint32_t*>(b + o_pairs);
-  r->q_lo.assign(d->q_lo, d->q_lo + D);
-  r->q_hi.assign(d->q_hi, d->q_hi + D);
+  for (int j = 0; j < D; ++j) {
+    r->q_lo[j] = d->q_lo[j];
+    r->q_hi[j] = d->q_hi[j];
+  }
   *out = r;
   return CR_OK;
 }

@@ -54,6 +54,7 @@ struct EvalArgs {
   const ProblemView* problems;   // batched launch: device table, or nullptr
   const int4* tiles;             // batched launch: (problem, first traj, n traj, -)
   int n_tiles;
+  int* queue;                    // persistent launch: work counter (zeroed before launch), or nullptr
   int traj_per_tile;             // single-problem launch: trajectories per CTA
   int max_traj;                  // largest trajectory count of a tile
   int max_states;                // largest (trajectories x horizon) of a tile
@@ -120,7 +121,23 @@ cudaError_t launch_fk(const RobotView& rb, const float* theta, int n, float* sph
                       float* link_tf, cudaStream_t stream);
 cudaError_t launch_eval(const EvalArgs& a, int grid, int block, cudaStream_t stream);
 int eval_smem_bytes(const EvalArgs& a, int block);
+int eval_blocks_per_sm(const EvalArgs& a, int block);
 cudaError_t launch_opt(const OptArgs& a, int n_max, cudaStream_t stream);
 int opt_smem_bytes(int history, int n_max);
 
+cr_status set_error(cr_status code, const char* msg);
+
 }  // namespace crgb
+
+// Handle types of the public ABI (opaque to callers).
+struct cr_robot {
+  int dof = 0, n_spheres = 0, n_pairs = 0;
+  void* dev = nullptr;
+  crgb::RobotView view{};
+  float q_lo[CR_MAX_DOF], q_hi[CR_MAX_DOF];
+};
+
+struct cr_world {
+  int n = 0;
+  crgb::BoxRows* dev = nullptr;
+};

@@ -227,7 +227,16 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
   const int n_tiles = a.problems ? a.n_tiles
                                  : (a.prob0.n_traj + a.traj_per_tile - 1) / a.traj_per_tile;
 
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  // Tiles are taken in order from a device counter (persistent launch over
+  // uneven problems) or strided by the grid.
+  __shared__ int s_next;
+  int tile = blockIdx.x;
+  if (a.queue) {
+    if (tid == 0) s_next = atomicAdd(a.queue, 1);
+    __syncthreads();
+    tile = s_next;
+  }
+  for (; tile < n_tiles;) {
     const ProblemView* pv;
     int r0, nt;
     if (a.problems) {
@@ -636,6 +645,14 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
         }
       }
     }
+    if (a.queue) {
+      __syncthreads();
+      if (tid == 0) s_next = atomicAdd(a.queue, 1);
+      __syncthreads();
+      tile = s_next;
+    } else {
+      tile += gridDim.x;
+    }
   }
 }
 
@@ -676,6 +693,34 @@ __global__ void k_fk(RobotView rb, const float* __restrict__ theta, int n, float
 
 }  // namespace
 
+// The largest dynamic shared memory any launch may ask for (227 KB) is set
+// once per kernel and device, never lowered, so launches captured in a graph
+// stay valid whatever is launched later.
+template <int DMAX>
+cudaError_t allow_eval_smem() {
+  static unsigned done = 0;  // bit per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned bit = 1u << (dev & 31);
+  if (done & bit) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_eval<DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) done |= bit;
+  return e;
+}
+
+int eval_blocks_per_sm(const EvalArgs& a, int block) {
+  const int smem = eval_smem_bytes(a, block);
+  int n = 0;
+  if (a.rb.dof <= 8) {
+    allow_eval_smem<8>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval<8>, block, smem);
+  } else {
+    allow_eval_smem<16>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval<16>, block, smem);
+  }
+  return n;
+}
+
 int eval_smem_bytes(const EvalArgs& a, int block) {
   EvalSmem L;
   L.build(a.rb.dof, a.rb.n_spheres, a.rb.n_pairs, a.max_traj, a.max_states, a.max_horizon,
@@ -686,11 +731,11 @@ int eval_smem_bytes(const EvalArgs& a, int block) {
 cudaError_t launch_eval(const EvalArgs& a, int grid, int block, cudaStream_t stream) {
   const int smem = eval_smem_bytes(a, block);
   if (a.rb.dof <= 8) {
-    cudaError_t e = cudaFuncSetAttribute(k_eval<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_eval_smem<8>();
     if (e != cudaSuccess) return e;
     k_eval<8><<<grid, block, smem, stream>>>(a);
   } else {
-    cudaError_t e = cudaFuncSetAttribute(k_eval<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_eval_smem<16>();
     if (e != cudaSuccess) return e;
     k_eval<16><<<grid, block, smem, stream>>>(a);
   }

@@ -4,9 +4,15 @@
 // A seed's history (m pairs of n = H*dof floats) is pulled into shared memory
 // with one bulk load, so the 2m dependent dot products of the two-loop
 // recursion run out of shared memory; the history shift is a relabelling of
-// slots while the pairs are written back in newest-last order.  Every dot
-// product is a fixed-shape block reduction (lane sums, xor butterfly, warp
-// partials summed in warp order), so the result does not depend on timing.
+// slots while the pairs are written back in newest-last order.
+//
+// Every dot product is reduced in one fixed order, that of a virtual block of
+// 256 threads: element k belongs to virtual thread k mod 256, which adds its
+// elements k, k + 256, ... in sequence (fma); lanes of a virtual warp are then
+// combined by an xor butterfly and the 8 virtual-warp sums are added in warp
+// order.  Seeds of up to 256 variables may run on a single warp (each lane
+// playing 8 virtual threads) with bit-identical results, so a seed's result
+// never depends on the other seeds of the launch.
 #include <cuda_runtime.h>
 
 #include "crgb_internal.cuh"
@@ -15,38 +21,70 @@ namespace crgb {
 
 namespace {
 
-constexpr int kMaxPerThread = 8;  // n <= 8 * threads variables per seed
+constexpr int kVirt = 256;        // virtual threads per seed
+constexpr int kSlots = 8;         // element slots per physical thread
+constexpr int kMaxN = kVirt * kSlots;
 
-// Sum V values over the block of NT threads; every thread gets the totals.
-template <int NT, int V>
-__device__ __forceinline__ void block_sum(float (&v)[V], float* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Partial sums of one dot product for NT physical threads.
+template <int NT>
+struct Part {
+  static constexpr int kP = NT == kVirt ? 1 : kSlots;
+  float p[kP];
+  __device__ __forceinline__ void zero() {
 #pragma unroll
-  for (int k = 0; k < V; ++k) {
-    float s = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    v[k] = s;
-    if (NT > 32 && lane == 0) red[warp * V + k] = s;
+    for (int i = 0; i < kP; ++i) p[i] = 0.f;
   }
-  if (NT > 32) {
+  // add a*b for element slot e (element k = tid + NT * e)
+  __device__ __forceinline__ void fma(int e, float a, float b) {
+    if (kP == 1)
+      p[0] = fmaf(a, b, p[0]);
+    else
+      p[e] = fmaf(a, b, p[e]);
+  }
+};
+
+__device__ __forceinline__ float butterfly(float s) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Totals of V dot products; every thread gets them.
+template <int NT, int V>
+__device__ __forceinline__ void block_sum(Part<NT> (&v)[V], float (&out)[V], float* red) {
+  if (NT == kVirt) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const float s = butterfly(v[k].p[0]);
+      if (lane == 0) red[warp * V + k] = s;
+    }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < V; ++k) {
       float s = 0.f;
-      for (int w = 0; w < NT / 32; ++w) s += red[w * V + k];
-      v[k] = s;
+      for (int w = 0; w < kVirt / 32; ++w) s += red[w * V + k];
+      out[k] = s;
     }
     __syncthreads();
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      float s = 0.f;
+#pragma unroll
+      for (int w = 0; w < kSlots; ++w) s += butterfly(v[k].p[w]);
+      out[k] = s;
+    }
   }
 }
 
-// NT threads per seed: 32 for short seeds (IK, n <= 256), 256 otherwise.
+// NT = 256 for any seed up to 2048 variables; NT = 32 for seeds of at most
+// 256 variables (IK), same numerics.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
-  constexpr int kOptThreads = NT;
+  static_assert(NT == 32 || NT == kVirt, "NT");
   extern __shared__ __align__(16) float osm[];
-  __shared__ float red[(NT / 32) * (CR_MAX_ALPHA + 1)];
+  __shared__ float red[(kVirt / 32) * (CR_MAX_ALPHA + 1)];
   __shared__ float sh_rho[CR_MAX_HISTORY];
   __shared__ float sh_alpha[CR_MAX_HISTORY];
 
@@ -75,25 +113,30 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
 
     // ---------------- line-search selection (Alg. 1) ----------------
     if (a.do_select) {
-      float v[CR_MAX_ALPHA + 1];
+      Part<NT> v[CR_MAX_ALPHA + 1];
 #pragma unroll
-      for (int l = 0; l <= CR_MAX_ALPHA; ++l) v[l] = 0.f;
-      for (int k = tid; k < n; k += kOptThreads) {
-        const float dk = dir[k];
-        v[0] = fmaf(g[k], dk, v[0]);
+      for (int l = 0; l <= CR_MAX_ALPHA; ++l) v[l].zero();
 #pragma unroll
-        for (int l = 0; l < CR_MAX_ALPHA; ++l)
-          if (l < na) v[1 + l] = fmaf(cgrad[(long long)l * n + k], dk, v[1 + l]);
+      for (int e = 0; e < kSlots; ++e) {
+        const int k = tid + NT * e;
+        if (k < n) {
+          const float dk = dir[k];
+          v[0].fma(e, g[k], dk);
+#pragma unroll
+          for (int l = 0; l < CR_MAX_ALPHA; ++l)
+            if (l < na) v[1 + l].fma(e, cgrad[(long long)l * n + k], dk);
+        }
       }
-      block_sum<NT, CR_MAX_ALPHA + 1>(v, red);
+      float tot[CR_MAX_ALPHA + 1];
+      block_sum<NT, CR_MAX_ALPHA + 1>(v, tot, red);
       const float c0 = st.c[b];
-      const float gd0 = v[0];
+      const float gd0 = tot[0];
       int idx = 0;
       for (int l = 0; l < na; ++l) {
         const float cl = st.cand_cost[b * na + l];
         bool ok = cl <= c0 + a.prm.armijo_c1 * a.prm.alpha[l] * gd0;
         if (a.prm.flags & CR_WOLFE) {
-          const float gld = v[1 + l];
+          const float gld = tot[1 + l];
           if (a.prm.flags & CR_STRONG_WOLFE)
             ok = ok && fabsf(gld) <= a.prm.wolfe_c2 * fabsf(gd0);
           else
@@ -103,11 +146,15 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
       }
       const float cnew = st.cand_cost[b * na + idx];
       const bool better = cnew < st.best_c[b];  // NaN never improves the best
-      for (int k = tid; k < n; k += kOptThreads) {
-        const float xv = cand[(long long)idx * n + k];
-        x[k] = xv;
-        g[k] = cgrad[(long long)idx * n + k];
-        if (better) st.best_x[vo + k] = xv;
+#pragma unroll
+      for (int e = 0; e < kSlots; ++e) {
+        const int k = tid + NT * e;
+        if (k < n) {
+          const float xv = cand[(long long)idx * n + k];
+          x[k] = xv;
+          g[k] = cgrad[(long long)idx * n + k];
+          if (better) st.best_x[vo + k] = xv;
+        }
       }
       __syncthreads();  // every thread has read c[b] and best_c[b]
       if (tid == 0) {
@@ -120,75 +167,77 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
       }
     }
     if (a.init_best) {
-      for (int k = tid; k < n; k += kOptThreads) st.best_x[vo + k] = x[k];
+      for (int k = tid; k < n; k += NT) st.best_x[vo + k] = x[k];
       if (tid == 0) st.best_c[b] = st.c[b];
     }
 
     // ---------------- L-BFGS step (App. A.7) ----------------
     if (a.do_propose) {
-      float* hs = osm;                 // [m][n] s pairs, physical slots
-      float* hy = osm + (size_t)m * n; // [m][n]
+      float* hs = osm;                  // [m][n] s pairs, physical slots
+      float* hy = osm + (size_t)m * n;  // [m][n]
       float* s_g = st.s + (long long)vo * m;
       float* y_g = st.y + (long long)vo * m;
       float* rho_g = st.rho + b * m;
-      for (int k = tid; k < m * n; k += kOptThreads) {
+      for (int k = tid; k < m * n; k += NT) {
         hs[k] = s_g[k];
         hy[k] = y_g[k];
       }
       if (tid < m) sh_rho[tid] = rho_g[tid];
       const int it = st.iter[b];
-      float xr[kMaxPerThread], gr[kMaxPerThread];
+      float xr[kSlots], gr[kSlots];
 #pragma unroll
-      for (int u = 0; u < kMaxPerThread; ++u) {
-        const int k = tid + u * kOptThreads;
-        xr[u] = k < n ? x[k] : 0.f;
-        gr[u] = k < n ? g[k] : 0.f;
+      for (int e = 0; e < kSlots; ++e) {
+        const int k = tid + NT * e;
+        xr[e] = k < n ? x[k] : 0.f;
+        gr[e] = k < n ? g[k] : 0.f;
       }
       __syncthreads();
       int shift = 0;  // logical pair i (0 = oldest) lives in physical slot (i + shift) % m
       if (it > 0) {
         // the newest pair overwrites the oldest slot (physical 0)
-        float sv[kMaxPerThread], yv[kMaxPerThread];
-        float ys[1] = {0.f};
+        float sv[kSlots], yv[kSlots];
+        Part<NT> ys[1];
+        ys[0].zero();
 #pragma unroll
-        for (int u = 0; u < kMaxPerThread; ++u) {
-          const int k = tid + u * kOptThreads;
-          sv[u] = k < n ? xr[u] - xp[k] : 0.f;
-          yv[u] = k < n ? gr[u] - gp[k] : 0.f;
-          ys[0] = fmaf(yv[u], sv[u], ys[0]);
+        for (int e = 0; e < kSlots; ++e) {
+          const int k = tid + NT * e;
+          sv[e] = k < n ? xr[e] - xp[k] : 0.f;
+          yv[e] = k < n ? gr[e] - gp[k] : 0.f;
+          if (k < n) ys[0].fma(e, yv[e], sv[e]);
         }
-        block_sum<NT, 1>(ys, red);
+        float yst[1];
+        block_sum<NT, 1>(ys, yst, red);
 #pragma unroll
-        for (int u = 0; u < kMaxPerThread; ++u) {
-          const int k = tid + u * kOptThreads;
+        for (int e = 0; e < kSlots; ++e) {
+          const int k = tid + NT * e;
           if (k < n) {
-            hs[k] = sv[u];
-            hy[k] = yv[u];
+            hs[k] = sv[e];
+            hy[k] = yv[e];
           }
         }
-        if (tid == 0) sh_rho[0] = ys[0] > 1e-8f ? 1.f / ys[0] : 0.f;
+        if (tid == 0) sh_rho[0] = yst[0] > 1e-8f ? 1.f / yst[0] : 0.f;
         shift = 1;
         __syncthreads();
         // write back newest-last
         for (int i = 0; i < m; ++i) {
           const int p = (i + shift) % m;
-          for (int k = tid; k < n; k += kOptThreads) {
+          for (int k = tid; k < n; k += NT) {
             s_g[(long long)i * n + k] = hs[(long long)p * n + k];
             y_g[(long long)i * n + k] = hy[(long long)p * n + k];
           }
         }
         if (tid < m) rho_g[tid] = sh_rho[(tid + shift) % m];
       }
-      for (int k = tid; k < n; k += kOptThreads) {
+      for (int k = tid; k < n; k += NT) {
         xp[k] = x[k];
         gp[k] = g[k];
       }
       if (tid == 0) st.iter[b] = it + 1;
 
       // two-loop recursion: q = g; newest to oldest
-      float q[kMaxPerThread];
+      float q[kSlots];
 #pragma unroll
-      for (int u = 0; u < kMaxPerThread; ++u) q[u] = gr[u];
+      for (int e = 0; e < kSlots; ++e) q[e] = gr[e];
       for (int i = m - 1; i >= 0; --i) {
         const int p = (i + shift) % m;
         const float rho = sh_rho[p];
@@ -196,19 +245,21 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
           if (tid == 0) sh_alpha[i] = 0.f;
           continue;
         }
-        float d[1] = {0.f};
+        Part<NT> d[1];
+        d[0].zero();
 #pragma unroll
-        for (int u = 0; u < kMaxPerThread; ++u) {
-          const int k = tid + u * kOptThreads;
-          if (k < n) d[0] = fmaf(hs[(long long)p * n + k], q[u], d[0]);
+        for (int e = 0; e < kSlots; ++e) {
+          const int k = tid + NT * e;
+          if (k < n) d[0].fma(e, hs[(long long)p * n + k], q[e]);
         }
-        block_sum<NT, 1>(d, red);
-        const float al = rho * d[0];
+        float dt[1];
+        block_sum<NT, 1>(d, dt, red);
+        const float al = rho * dt[0];
         if (tid == 0) sh_alpha[i] = al;
 #pragma unroll
-        for (int u = 0; u < kMaxPerThread; ++u) {
-          const int k = tid + u * kOptThreads;
-          if (k < n) q[u] = fmaf(-al, hy[(long long)p * n + k], q[u]);
+        for (int e = 0; e < kSlots; ++e) {
+          const int k = tid + NT * e;
+          if (k < n) q[e] = fmaf(-al, hy[(long long)p * n + k], q[e]);
         }
       }
       // H0 = gamma I from the newest valid pair
@@ -216,53 +267,58 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
       for (int i = m - 1; i >= 0; --i) {
         const int p = (i + shift) % m;
         if (sh_rho[p] > 0.f) {
-          float d[2] = {0.f, 0.f};
+          Part<NT> d[2];
+          d[0].zero();
+          d[1].zero();
 #pragma unroll
-          for (int u = 0; u < kMaxPerThread; ++u) {
-            const int k = tid + u * kOptThreads;
+          for (int e = 0; e < kSlots; ++e) {
+            const int k = tid + NT * e;
             if (k < n) {
               const float sv = hs[(long long)p * n + k], yv = hy[(long long)p * n + k];
-              d[0] = fmaf(sv, yv, d[0]);
-              d[1] = fmaf(yv, yv, d[1]);
+              d[0].fma(e, sv, yv);
+              d[1].fma(e, yv, yv);
             }
           }
-          block_sum<NT, 2>(d, red);
-          gamma = d[0] / d[1];
+          float dt[2];
+          block_sum<NT, 2>(d, dt, red);
+          gamma = dt[0] / dt[1];
           break;
         }
       }
 #pragma unroll
-      for (int u = 0; u < kMaxPerThread; ++u) q[u] *= gamma;
+      for (int e = 0; e < kSlots; ++e) q[e] *= gamma;
       __syncthreads();  // sh_alpha visible
       for (int i = 0; i < m; ++i) {
         const int p = (i + shift) % m;
         const float rho = sh_rho[p];
         if (rho == 0.f) continue;
-        float d[1] = {0.f};
+        Part<NT> d[1];
+        d[0].zero();
 #pragma unroll
-        for (int u = 0; u < kMaxPerThread; ++u) {
-          const int k = tid + u * kOptThreads;
-          if (k < n) d[0] = fmaf(hy[(long long)p * n + k], q[u], d[0]);
+        for (int e = 0; e < kSlots; ++e) {
+          const int k = tid + NT * e;
+          if (k < n) d[0].fma(e, hy[(long long)p * n + k], q[e]);
         }
-        block_sum<NT, 1>(d, red);
-        const float coef = sh_alpha[i] - rho * d[0];
+        float dt[1];
+        block_sum<NT, 1>(d, dt, red);
+        const float coef = sh_alpha[i] - rho * dt[0];
 #pragma unroll
-        for (int u = 0; u < kMaxPerThread; ++u) {
-          const int k = tid + u * kOptThreads;
-          if (k < n) q[u] = fmaf(hs[(long long)p * n + k], coef, q[u]);
+        for (int e = 0; e < kSlots; ++e) {
+          const int k = tid + NT * e;
+          if (k < n) q[e] = fmaf(hs[(long long)p * n + k], coef, q[e]);
         }
       }
       // direction and the clipped candidates of Alg. 1
 #pragma unroll
-      for (int u = 0; u < kMaxPerThread; ++u) {
-        const int k = tid + u * kOptThreads;
+      for (int e = 0; e < kSlots; ++e) {
+        const int k = tid + NT * e;
         if (k < n) {
-          const float dk = -q[u];
+          const float dk = -q[e];
           dir[k] = dk;
           const int j = k % D;
           const float lo = a.q_lo[j], hi = a.q_hi[j];
           for (int l = 0; l < na; ++l) {
-            float v = fmaf(a.prm.alpha[l], dk, xr[u]);
+            float v = fmaf(a.prm.alpha[l], dk, xr[e]);
             v = fminf(fmaxf(v, lo), hi);
             cand[(long long)l * n + k] = v;
           }
@@ -272,21 +328,37 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
   }
 }
 
+// The largest dynamic shared memory any launch may ask for is set once per
+// kernel and device (never lowered), so launches captured in a graph stay
+// valid whatever is launched later.
+template <int NT>
+cudaError_t allow_opt_smem() {
+  static unsigned done = 0;  // bit per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned bit = 1u << (dev & 31);
+  if (done & bit) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_opt<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess) done |= bit;
+  return e;
+}
+
 }  // namespace
 
 int opt_smem_bytes(int history, int n_max) { return 2 * history * n_max * (int)sizeof(float); }
 
 cudaError_t launch_opt(const OptArgs& a, int n_max, cudaStream_t stream) {
   if (a.n_seeds <= 0) return cudaSuccess;
+  if (n_max > kMaxN) return cudaErrorInvalidValue;
   const int smem = a.do_propose ? opt_smem_bytes(a.prm.history, n_max) : 0;
-  if (n_max <= 32 * kMaxPerThread) {
-    cudaError_t e = cudaFuncSetAttribute(k_opt<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (n_max <= kVirt) {
+    cudaError_t e = allow_opt_smem<32>();
     if (e != cudaSuccess) return e;
     k_opt<32><<<a.n_seeds, 32, smem, stream>>>(a);
   } else {
-    cudaError_t e = cudaFuncSetAttribute(k_opt<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_opt_smem<kVirt>();
     if (e != cudaSuccess) return e;
-    k_opt<256><<<a.n_seeds, 256, smem, stream>>>(a);
+    k_opt<kVirt><<<a.n_seeds, kVirt, smem, stream>>>(a);
   }
   return cudaGetLastError();
 }

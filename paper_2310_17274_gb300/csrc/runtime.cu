@@ -1,0 +1,489 @@
+// runtime.cu -- context, workspace and the batched, graph-captured solve of
+// many uneven problems (Sec. 4.1: iterations of L-BFGS + parallel noisy line
+// search with best-iterate tracking; App. D: iterations captured in a CUDA
+// graph).
+//
+// Layout of a batch of P problems (problem p: B_p seeds, horizon H_p, n_p =
+// H_p * dof variables per seed): per-seed arrays are concatenated problem by
+// problem, so seed b of problem p starts at float offset vo_p + b n_p; the
+// n_alpha line-search candidates of a seed are contiguous ([B_p][n_alpha][n_p]
+// per problem).  One evaluation launch covers every problem: a tile table
+// lists (problem, first trajectory, count) and CTAs take tiles from a device
+// counter, largest tiles first.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "crgb_internal.cuh"
+
+using namespace crgb;
+
+namespace crgb {
+cr_status check_params(const cr_params* p);
+cr_status fill_problem(const cr_robot* rb, const cr_problem* pr, ProblemView* pv);
+}  // namespace crgb
+
+namespace {
+
+cr_status failf(cr_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  return set_error(code, buf);
+}
+
+#define RT_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) return failf(CR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// per-problem output pointers for the finishing kernel
+struct ResultView {
+  float* traj;
+  float* cost;
+  uint8_t* cfree;
+  int* best;
+  int n_seeds, n, seed_base, var_base;
+};
+
+// Best seed per problem: the lowest-cost collision-free seed, else the
+// lowest-cost seed (App. A.9 picks among valid seeds); copy out every seed's
+// best iterate, cost and flag.
+__global__ void k_finish(const ResultView* res, int n_problems, const float* best_x,
+                         const float* best_c, const uint8_t* best_cfree) {
+  const int p = blockIdx.x;
+  if (p >= n_problems) return;
+  const ResultView r = res[p];
+  __shared__ int s_best;
+  if (threadIdx.x == 0) {
+    int bi = 0, bf = -1;
+    float bc = INFINITY, fc = INFINITY;
+    for (int b = 0; b < r.n_seeds; ++b) {
+      const float c = best_c[r.seed_base + b];
+      if (c < bc) {
+        bc = c;
+        bi = b;
+      }
+      if (best_cfree[r.seed_base + b] && (bf < 0 || c < fc)) {
+        fc = c;
+        bf = b;
+      }
+    }
+    s_best = bf >= 0 ? bf : bi;
+    if (r.best) *r.best = s_best;
+  }
+  __syncthreads();
+  const long long total = (long long)r.n_seeds * r.n;
+  if (r.traj)
+    for (long long k = threadIdx.x; k < total; k += blockDim.x) r.traj[k] = best_x[r.var_base + k];
+  for (int b = threadIdx.x; b < r.n_seeds; b += blockDim.x) {
+    if (r.cost) r.cost[b] = best_c[r.seed_base + b];
+    if (r.cfree) r.cfree[b] = best_cfree[r.seed_base + b];
+  }
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e == cudaSuccess) bytes = need;
+    return e;
+  }
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+}  // namespace
+
+// Plan of one batch: tables, workspace carve-up and launch shapes.
+struct Plan {
+  int P = 0, S = 0, dof = 0, m = 0, na = 0;
+  long long V = 0;
+  int n_max = 0;
+  std::vector<ProblemView> probs_x, probs_c;
+  std::vector<int4> tiles_x, tiles_c, seedtab;
+  std::vector<ResultView> results;
+  int max_traj_x = 0, max_states_x = 0, max_traj_c = 0, max_states_c = 0, max_h = 0;
+  // workspace offsets (bytes)
+  size_t o_x, o_g, o_xp, o_gp, o_dir, o_bx, o_c, o_bc, o_rho, o_it, o_s, o_y, o_cand, o_cgrad,
+      o_ccost, o_cfree, o_bfree, o_ls, o_queue, ws_bytes;
+  size_t o_tx, o_tc, o_px, o_pc, o_seed, o_res, tab_bytes;
+};
+
+struct cr_ctx {
+  int device = 0;
+  size_t mem_budget = 0;
+  int n_sm = 0;
+  cudaStream_t cap = nullptr;
+  DevBuf ws, tab;
+  std::vector<unsigned char> tab_host;
+  unsigned char* tab_pinned = nullptr;
+  size_t tab_pinned_bytes = 0;
+  cudaEvent_t staged = nullptr;  // recorded after the last copy out of tab_pinned
+  int block = 256;
+  // graph cache: key bytes -> executable graph
+  std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
+  // autotune table: key (M, K bucket, H) -> (block, trajectories per tile for short horizons)
+  std::map<long long, int2> tune;
+  ~cr_ctx() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+    if (cap) cudaStreamDestroy(cap);
+    if (tab_pinned) cudaFreeHost(tab_pinned);
+    if (staged) cudaEventDestroy(staged);
+  }
+};
+
+namespace {
+
+int traj_per_tile(int H) { return H >= 32 ? 1 : (32 + H - 1) / H; }
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* pr,
+                     const cr_params* prm, const cr_result* res, Plan& pl) {
+  pl.P = P;
+  pl.dof = rb->dof;
+  pl.m = prm->history;
+  pl.na = prm->n_alpha;
+  pl.probs_x.resize(P);
+  pl.probs_c.resize(P);
+  pl.results.resize(P);
+  long long vo = 0;
+  int sb = 0;
+  for (int p = 0; p < P; ++p) {
+    if (pr[p].n_seeds < 1) return failf(CR_EINVAL, "problem %d: n_seeds < 1", p);
+    ProblemView pv;
+    cr_status s = fill_problem(rb, &pr[p], &pv);
+    if (s != CR_OK) return s;
+    const int H = pr[p].horizon, B = pr[p].n_seeds, n = H * rb->dof;
+    if (n > 2048) return failf(CR_EINVAL, "problem %d: horizon * dof = %d > 2048", p, n);
+    pl.n_max = std::max(pl.n_max, n);
+    pl.max_h = std::max(pl.max_h, H);
+    pv.n_traj = B;
+    pv.traj_base = sb;
+    pv.var_base = vo;
+    pl.probs_x[p] = pv;
+    ProblemView pc = pv;
+    pc.n_traj = B * pl.na;
+    pc.traj_base = sb * pl.na;
+    pc.var_base = vo * pl.na;
+    pl.probs_c[p] = pc;
+    for (int b = 0; b < B; ++b) pl.seedtab.push_back(make_int4(n, (int)(vo + (long long)b * n), p, 0));
+    ResultView rv;
+    rv.traj = res ? res[p].traj : nullptr;
+    rv.cost = res ? res[p].cost : nullptr;
+    rv.cfree = res ? res[p].cfree : nullptr;
+    rv.best = res ? res[p].best : nullptr;
+    rv.n_seeds = B;
+    rv.n = n;
+    rv.seed_base = sb;
+    rv.var_base = (int)vo;
+    pl.results[p] = rv;
+    vo += (long long)B * n;
+    sb += B;
+  }
+  pl.S = sb;
+  pl.V = vo;
+  if (pl.V * pl.na > (1ll << 31) - 1) return failf(CR_EINVAL, "batch too large");
+  // tiles, largest first (cost ~ states x boxes), so a counter-driven
+  // persistent launch ends with small tiles
+  auto make_tiles = [&](const std::vector<ProblemView>& pvs, std::vector<int4>& tiles, int& mt,
+                        int& ms) {
+    std::vector<std::pair<long long, int4>> tmp;
+    for (int p = 0; p < P; ++p) {
+      const int H = pvs[p].horizon, nt = traj_per_tile(H);
+      for (int r0 = 0; r0 < pvs[p].n_traj; r0 += nt) {
+        const int c = std::min(nt, pvs[p].n_traj - r0);
+        tmp.push_back({(long long)c * H * (pvs[p].n_boxes + 8), make_int4(p, r0, c, 0)});
+        mt = std::max(mt, c);
+        ms = std::max(ms, c * H);
+      }
+    }
+    std::stable_sort(tmp.begin(), tmp.end(),
+                     [](const std::pair<long long, int4>& a, const std::pair<long long, int4>& b) {
+                       return a.first > b.first;
+                     });
+    tiles.clear();
+    for (auto& t : tmp) tiles.push_back(t.second);
+  };
+  make_tiles(pl.probs_x, pl.tiles_x, pl.max_traj_x, pl.max_states_x);
+  make_tiles(pl.probs_c, pl.tiles_c, pl.max_traj_c, pl.max_states_c);
+  // workspace
+  const size_t V = (size_t)pl.V, S = (size_t)pl.S, m = pl.m, na = pl.na;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
+  pl.o_x = take(V * 4); pl.o_g = take(V * 4); pl.o_xp = take(V * 4); pl.o_gp = take(V * 4);
+  pl.o_dir = take(V * 4); pl.o_bx = take(V * 4); pl.o_c = take(S * 4); pl.o_bc = take(S * 4);
+  pl.o_rho = take(S * m * 4); pl.o_it = take(S * 4); pl.o_s = take(V * m * 4);
+  pl.o_y = take(V * m * 4); pl.o_cand = take(V * na * 4); pl.o_cgrad = take(V * na * 4);
+  pl.o_ccost = take(S * na * 4); pl.o_cfree = take(S * na); pl.o_bfree = take(S);
+  pl.o_ls = take(S * 4); pl.o_queue = take(256);
+  pl.ws_bytes = o;
+  o = 0;
+  pl.o_tx = take(pl.tiles_x.size() * sizeof(int4));
+  pl.o_tc = take(pl.tiles_c.size() * sizeof(int4));
+  pl.o_px = take(P * sizeof(ProblemView));
+  pl.o_pc = take(P * sizeof(ProblemView));
+  pl.o_seed = take(pl.seedtab.size() * sizeof(int4));
+  pl.o_res = take(P * sizeof(ResultView));
+  pl.tab_bytes = o;
+  if (ctx->mem_budget && pl.ws_bytes + pl.tab_bytes > ctx->mem_budget)
+    return failf(CR_ENOMEM, "batch needs %zu bytes > context budget %zu", pl.ws_bytes + pl.tab_bytes,
+                 ctx->mem_budget);
+  return CR_OK;
+}
+
+cr_opt_state state_of(const Plan& pl, unsigned char* ws) {
+  cr_opt_state st;
+  std::memset(&st, 0, sizeof(st));
+  st.n_seeds = pl.S;
+  st.horizon = 0;
+  st.x = (float*)(ws + pl.o_x);
+  st.g = (float*)(ws + pl.o_g);
+  st.c = (float*)(ws + pl.o_c);
+  st.x_prev = (float*)(ws + pl.o_xp);
+  st.g_prev = (float*)(ws + pl.o_gp);
+  st.s = (float*)(ws + pl.o_s);
+  st.y = (float*)(ws + pl.o_y);
+  st.rho = (float*)(ws + pl.o_rho);
+  st.iter = (int32_t*)(ws + pl.o_it);
+  st.dir = (float*)(ws + pl.o_dir);
+  st.cand = (float*)(ws + pl.o_cand);
+  st.cand_cost = (float*)(ws + pl.o_ccost);
+  st.cand_grad = (float*)(ws + pl.o_cgrad);
+  st.cand_cfree = (uint8_t*)(ws + pl.o_cfree);
+  st.best_x = (float*)(ws + pl.o_bx);
+  st.best_c = (float*)(ws + pl.o_bc);
+  st.best_cfree = (uint8_t*)(ws + pl.o_bfree);
+  st.ls_index = (int32_t*)(ws + pl.o_ls);
+  return st;
+}
+
+// Enqueue the iterations on `s` (eagerly or under capture).
+cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* prm, const Plan& pl,
+                             unsigned char* ws, unsigned char* tab, int iters, bool persistent,
+                             cudaStream_t s) {
+  const cr_opt_state st = state_of(pl, ws);
+  int* queue = (int*)(ws + pl.o_queue);
+  auto eval_args = [&](bool cand) {
+    EvalArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.rb = rb->view;
+    a.prm = *prm;
+    a.problems = (const ProblemView*)(tab + (cand ? pl.o_pc : pl.o_px));
+    a.tiles = (const int4*)(tab + (cand ? pl.o_tc : pl.o_tx));
+    a.n_tiles = (int)(cand ? pl.tiles_c.size() : pl.tiles_x.size());
+    a.max_traj = cand ? pl.max_traj_c : pl.max_traj_x;
+    a.max_states = cand ? pl.max_states_c : pl.max_states_x;
+    a.max_horizon = pl.max_h;
+    a.theta = cand ? st.cand : st.x;
+    a.cost = cand ? st.cand_cost : st.c;
+    a.grad = cand ? st.cand_grad : st.g;
+    a.cfree = cand ? st.cand_cfree : st.best_cfree;
+    a.terms = nullptr;
+    a.queue = persistent ? queue : nullptr;
+    return a;
+  };
+  auto launch_eval_batch = [&](bool cand) -> cr_status {
+    EvalArgs a = eval_args(cand);
+    const int block = ctx->block;
+    const int smem = eval_smem_bytes(a, block);
+    if (smem > 227 * 1024) return failf(CR_EINVAL, "tile needs %d bytes of shared memory", smem);
+    int grid = a.n_tiles;
+    if (persistent) {
+      const int per_sm = std::max(1, eval_blocks_per_sm(a, block));
+      grid = std::min(a.n_tiles, per_sm * ctx->n_sm);
+      RT_CUDA(cudaMemsetAsync(queue, 0, sizeof(int), s));
+    }
+    RT_CUDA(launch_eval(a, grid, block, s));
+    return CR_OK;
+  };
+  OptArgs o;
+  std::memset(&o, 0, sizeof(o));
+  o.prm = *prm;
+  o.q_lo = rb->view.lim;
+  o.q_hi = rb->view.lim + rb->dof;
+  o.dof = rb->dof;
+  o.n_seeds = pl.S;
+  o.seed_tab = (const int4*)(tab + pl.o_seed);
+  o.st = st;
+
+  // iteration state starts empty
+  RT_CUDA(cudaMemsetAsync(st.s, 0, (size_t)pl.V * pl.m * 4, s));
+  RT_CUDA(cudaMemsetAsync(st.y, 0, (size_t)pl.V * pl.m * 4, s));
+  RT_CUDA(cudaMemsetAsync(st.rho, 0, (size_t)pl.S * pl.m * 4, s));
+  RT_CUDA(cudaMemsetAsync(st.iter, 0, (size_t)pl.S * 4, s));
+  cr_status rs = launch_eval_batch(false);
+  if (rs != CR_OK) return rs;
+  o.init_best = 1;
+  o.do_propose = iters > 0;
+  RT_CUDA(launch_opt(o, pl.n_max, s));
+  o.init_best = 0;
+  for (int it = 0; it < iters; ++it) {
+    rs = launch_eval_batch(true);
+    if (rs != CR_OK) return rs;
+    o.do_select = 1;
+    o.do_propose = it + 1 < iters;
+    RT_CUDA(launch_opt(o, pl.n_max, s));
+  }
+  k_finish<<<pl.P, 256, 0, s>>>((const ResultView*)(tab + pl.o_res), pl.P, st.best_x, st.best_c,
+                                st.best_cfree);
+  RT_CUDA(cudaGetLastError());
+  return CR_OK;
+}
+
+std::string graph_key(const cr_robot* rb, const cr_params* prm, const Plan& pl, int iters,
+                      bool persistent, const void* ws, const void* tab, int block) {
+  std::string k;
+  auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
+  put(&rb, sizeof(rb));
+  put(prm, sizeof(*prm));
+  put(&iters, sizeof(iters));
+  put(&persistent, sizeof(persistent));
+  put(&ws, sizeof(ws));
+  put(&tab, sizeof(tab));
+  put(&block, sizeof(block));
+  put(&pl.P, sizeof(int));
+  for (int p = 0; p < pl.P; ++p) {
+    int shp[3] = {pl.probs_x[p].n_traj, pl.probs_x[p].horizon, pl.probs_x[p].n_boxes};
+    put(shp, sizeof(shp));
+  }
+  return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+cr_status cr_context_create(int device, size_t mem_budget, cr_ctx** out) {
+  if (!out) return failf(CR_EINVAL, "cr_context_create: null out");
+  *out = nullptr;
+  int n = 0;
+  RT_CUDA(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return failf(CR_EINVAL, "device %d not in 0..%d", device, n - 1);
+  RT_CUDA(cudaSetDevice(device));
+  cr_ctx* c = new cr_ctx();
+  c->device = device;
+  c->mem_budget = mem_budget;
+  cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
+  cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete c;
+    return failf(CR_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return CR_OK;
+}
+
+void cr_context_destroy(cr_ctx* c) { delete c; }
+
+cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
+                   const cr_params* params, int32_t iters, uint32_t solve_flags,
+                   const cr_result* results, void* stream) {
+  if (!ctx || !robot || !problems || n_problems < 1) return failf(CR_EINVAL, "cr_solve: bad argument");
+  if (iters < 0) return failf(CR_EINVAL, "cr_solve: iters < 0");
+  cr_status s = check_params(params);
+  if (s != CR_OK) return s;
+  for (int p = 0; p < n_problems; ++p)
+    if (!problems[p].seeds) return failf(CR_EINVAL, "problem %d: null seeds", p);
+  Plan pl;
+  s = build_plan(ctx, robot, n_problems, problems, params, results, pl);
+  if (s != CR_OK) return s;
+  if (opt_smem_bytes(params->history, pl.n_max) > 200 * 1024)
+    return failf(CR_EINVAL, "history * horizon * dof too large for shared memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  // a new workspace or table address invalidates the cached graphs
+  const void* ws0 = ctx->ws.p;
+  const void* tab0 = ctx->tab.p;
+  cudaError_t e = ctx->ws.ensure(pl.ws_bytes);
+  if (e != cudaSuccess) return failf(CR_ENOMEM, "workspace of %zu bytes: %s", pl.ws_bytes, cudaGetErrorString(e));
+  e = ctx->tab.ensure(pl.tab_bytes);
+  if (e != cudaSuccess) return failf(CR_ENOMEM, "tables of %zu bytes: %s", pl.tab_bytes, cudaGetErrorString(e));
+  if (ws0 != ctx->ws.p || tab0 != ctx->tab.p) {
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.second);
+    ctx->graphs.clear();
+  }
+  unsigned char* ws = (unsigned char*)ctx->ws.p;
+  unsigned char* tab = (unsigned char*)ctx->tab.p;
+  // tables through a pinned staging buffer; the previous call's copy out of
+  // it must have finished before it is rewritten
+  if (ctx->staged) RT_CUDA(cudaEventSynchronize(ctx->staged));
+  if (ctx->tab_pinned_bytes < pl.tab_bytes) {
+    if (ctx->tab_pinned) cudaFreeHost(ctx->tab_pinned);
+    ctx->tab_pinned = nullptr;
+    ctx->tab_pinned_bytes = 0;
+    RT_CUDA(cudaMallocHost(&ctx->tab_pinned, pl.tab_bytes));
+    ctx->tab_pinned_bytes = pl.tab_bytes;
+  }
+  if (!ctx->staged) RT_CUDA(cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming));
+  unsigned char* h = ctx->tab_pinned;
+  std::memcpy(h + pl.o_tx, pl.tiles_x.data(), pl.tiles_x.size() * sizeof(int4));
+  std::memcpy(h + pl.o_tc, pl.tiles_c.data(), pl.tiles_c.size() * sizeof(int4));
+  std::memcpy(h + pl.o_px, pl.probs_x.data(), pl.P * sizeof(ProblemView));
+  std::memcpy(h + pl.o_pc, pl.probs_c.data(), pl.P * sizeof(ProblemView));
+  std::memcpy(h + pl.o_seed, pl.seedtab.data(), pl.seedtab.size() * sizeof(int4));
+  std::memcpy(h + pl.o_res, pl.results.data(), pl.P * sizeof(ResultView));
+  RT_CUDA(cudaMemcpyAsync(tab, h, pl.tab_bytes, cudaMemcpyHostToDevice, st));
+  RT_CUDA(cudaEventRecord(ctx->staged, st));
+  // seeds -> x (host memory, or device memory with CR_SOLVE_DEVICE_SEEDS)
+  const cudaMemcpyKind kind =
+      (solve_flags & CR_SOLVE_DEVICE_SEEDS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (int p = 0; p < n_problems; ++p) {
+    const size_t bytes = (size_t)problems[p].n_seeds * problems[p].horizon * robot->dof * 4;
+    RT_CUDA(cudaMemcpyAsync(ws + pl.o_x + (size_t)pl.probs_x[p].var_base * 4, problems[p].seeds, bytes,
+                            kind, st));
+  }
+  const bool persistent = (solve_flags & CR_SOLVE_PERSISTENT) != 0;
+  if (!(solve_flags & CR_SOLVE_GRAPH)) {
+    return enqueue_iterations(ctx, robot, params, pl, ws, tab, iters, persistent, st);
+  }
+  const std::string key = graph_key(robot, params, pl, iters, persistent, ws, tab, ctx->block);
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : ctx->graphs)
+    if (g.first == key) exec = g.second;
+  if (!exec) {
+    // capture on the context's stream, ordered after the copies on `st`
+    cudaEvent_t ev;
+    RT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    RT_CUDA(cudaEventRecord(ev, st));
+    RT_CUDA(cudaStreamWaitEvent(ctx->cap, ev, 0));
+    cudaEventDestroy(ev);
+    RT_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    cr_status cs = enqueue_iterations(ctx, robot, params, pl, ws, tab, iters, persistent, ctx->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(ctx->cap, &graph);
+    if (cs != CR_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return cs;
+    }
+    if (ce != cudaSuccess) return failf(CR_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return failf(CR_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ce));
+    if (ctx->graphs.size() >= 8) {
+      cudaGraphExecDestroy(ctx->graphs.front().second);
+      ctx->graphs.erase(ctx->graphs.begin());
+    }
+    ctx->graphs.push_back({key, exec});
+  }
+  RT_CUDA(cudaGraphLaunch(exec, st));
+  return CR_OK;
+}
+
+}  // extern "C"
