@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI of include/crgb.h: handles, validation, launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -97,19 +98,68 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
   for (int i = 0; i < M; ++i)
     if (d->sphere_link[i] < 0 || d->sphere_link[i] >= D)
       return fail(CR_EINVAL, "sphere_link[%d] = %d not in 0..%d", i, d->sphere_link[i], D - 1);
-  std::vector<uint32_t> pairs(P);
   for (int p = 0; p < P; ++p) {
     int i = d->pairs[2 * p], j = d->pairs[2 * p + 1];
     if (i < 0 || i >= M || j < 0 || j >= M || i == j)
       return fail(CR_EINVAL, "pair %d = (%d, %d) invalid", p, i, j);
-    pairs[p] = (uint32_t)i | ((uint32_t)j << 16);
   }
-  // one blob: fixed_tf | lim | spheres (float4) | axis | link | pairs
+  // Bounding sphere of each link's enabled spheres (link frame): a lower
+  // bound on every distance of the link's spheres, used to skip whole links.
+  std::vector<float> lbs((size_t)D * 4, 0.f), soff(M, 0.f);
+  for (int l = 0; l < D; ++l) {
+    double c[3] = {0, 0, 0};
+    int cnt = 0;
+    for (int i = 0; i < M; ++i)
+      if (d->sphere_link[i] == l && d->spheres[4 * i + 3] >= 0.f) {
+        for (int a = 0; a < 3; ++a) c[a] += d->spheres[4 * i + a];
+        ++cnt;
+      }
+    double R = -1.0;
+    if (cnt > 0) {
+      for (int a = 0; a < 3; ++a) c[a] /= cnt;
+      for (int i = 0; i < M; ++i)
+        if (d->sphere_link[i] == l && d->spheres[4 * i + 3] >= 0.f) {
+          double dx = d->spheres[4 * i] - c[0], dy = d->spheres[4 * i + 1] - c[1],
+                 dz = d->spheres[4 * i + 2] - c[2];
+          double o = std::sqrt(dx * dx + dy * dy + dz * dz);
+          soff[i] = (float)(o * (1.0 + 1e-6) + 1e-6);  // rounded up: stays a bound in FP32
+          R = std::max(R, (double)soff[i] + d->spheres[4 * i + 3]);
+        }
+    }
+    for (int a = 0; a < 3; ++a) lbs[4 * l + a] = (float)c[a];
+    lbs[4 * l + 3] = (float)R;
+  }
+  // pairs grouped by link pair (stable), keeping each pair's original position
+  std::vector<int> order(P);
+  for (int p = 0; p < P; ++p) order[p] = p;
+  auto key = [&](int p) {
+    int a = d->sphere_link[d->pairs[2 * p]], b = d->sphere_link[d->pairs[2 * p + 1]];
+    return std::min(a, b) * kMaxDof + std::max(a, b);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key(x) < key(y); });
+  std::vector<uint32_t> pairs(P);
+  std::vector<int> orig(P);
+  std::vector<int4> groups;
+  for (int q = 0; q < P; ++q) {
+    const int p = order[q];
+    pairs[q] = (uint32_t)d->pairs[2 * p] | ((uint32_t)d->pairs[2 * p + 1] << 16);
+    orig[q] = p;
+    const int k = key(p);
+    if (groups.empty() || key(order[groups.back().z]) != k)
+      groups.push_back(make_int4(k / kMaxDof, k % kMaxDof, q, 0));
+    groups.back().w += 1;
+  }
+  const int G = (int)groups.size();
+  // one blob: fixed_tf | lim | spheres (float4) | axis | link | offsets | link spheres | pairs |
+  // original positions | groups
   const size_t n_fix = (size_t)(D + 1) * 12, n_lim = (size_t)5 * D;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t r = off; off = (off + bytes + 255) & ~size_t(255); return r; };
   const size_t o_fix = take(n_fix * 4), o_lim = take(n_lim * 4), o_sph = take((size_t)M * 16),
-               o_axis = take((size_t)D * 4), o_link = take((size_t)M * 4), o_pairs = take((size_t)(P > 0 ? P : 1) * 4);
+               o_axis = take((size_t)D * 4), o_link = take((size_t)M * 4),
+               o_soff = take((size_t)M * 4), o_lbs = take((size_t)D * 16),
+               o_pairs = take((size_t)(P > 0 ? P : 1) * 4), o_orig = take((size_t)(P > 0 ? P : 1) * 4),
+               o_grp = take((size_t)(G > 0 ? G : 1) * 16);
   std::vector<unsigned char> host(off, 0);
   std::memcpy(host.data() + o_fix, d->fixed_tf, n_fix * 4);
   float* lim = reinterpret_cast<float*>(host.data() + o_lim);
@@ -123,7 +173,13 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
   std::memcpy(host.data() + o_sph, d->spheres, (size_t)M * 16);
   std::memcpy(host.data() + o_axis, d->axis, (size_t)D * 4);
   std::memcpy(host.data() + o_link, d->sphere_link, (size_t)M * 4);
-  if (P > 0) std::memcpy(host.data() + o_pairs, pairs.data(), (size_t)P * 4);
+  std::memcpy(host.data() + o_soff, soff.data(), (size_t)M * 4);
+  std::memcpy(host.data() + o_lbs, lbs.data(), (size_t)D * 16);
+  if (P > 0) {
+    std::memcpy(host.data() + o_pairs, pairs.data(), (size_t)P * 4);
+    std::memcpy(host.data() + o_orig, orig.data(), (size_t)P * 4);
+  }
+  if (G > 0) std::memcpy(host.data() + o_grp, groups.data(), (size_t)G * 16);
   void* dev = nullptr;
   cudaError_t e = cudaMalloc(&dev, off);
   if (e != cudaSuccess) return fail(CR_ENOMEM, "cudaMalloc(%zu): %s", off, cudaGetErrorString(e));
@@ -147,6 +203,11 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
   r->view.axis = reinterpret_cast<const int*>(b + o_axis);
   r->view.sphere_link = reinterpret_cast<const int*>(b + o_link);
   r->view.pairs = reinterpret_cast<const uint32_t*>(b + o_pairs);
+  r->view.pair_orig = reinterpret_cast<const int*>(b + o_orig);
+  r->view.groups = reinterpret_cast<const int4*>(b + o_grp);
+  r->view.n_groups = G;
+  r->view.sphere_off = reinterpret_cast<const float*>(b + o_soff);
+  r->view.link_bs = reinterpret_cast<const float4*>(b + o_lbs);
   for (int j = 0; j < D; ++j) {
     r->q_lo[j] = d->q_lo[j];
     r->q_hi[j] = d->q_hi[j];
@@ -293,7 +354,7 @@ cr_status cr_eval(const cr_robot* robot, const cr_problem* problem, const cr_par
   a.terms = terms;
   const int block = 256;
   const int smem = eval_smem_bytes(a, block);
-  if (smem > 227 * 1024)
+  if (smem > eval_smem_limit())
     return fail(CR_EINVAL, "cr_eval: tile needs %d bytes of shared memory (> 227 KB)", smem);
   const int grid = (B + a.traj_per_tile - 1) / a.traj_per_tile;
   cudaError_t e = launch_eval(a, grid, block, (cudaStream_t)stream);

@@ -15,16 +15,22 @@ constexpr int kMaxPairs = 65535;
 constexpr int kMaxBoxes = 4096;
 constexpr int kMaxHorizon = 128;
 constexpr int kBoxChunk = 64;  // boxes staged in shared memory at a time
+constexpr int kSurvivors = 64; // (link, box) pairs a warp lists per round
 
 // Robot as the kernels see it (device pointers into one allocation).
 struct RobotView {
-  int dof, n_spheres, n_pairs;
+  int dof, n_spheres, n_pairs, n_groups;
   const float* fixed_tf;    // [(dof+1)*12]
   const int* axis;          // [dof]
   const float* lim;         // [5][dof]: q_lo, q_hi, v_max, a_max, j_max
   const float4* spheres;    // [M] centre (link frame), radius
   const int* sphere_link;   // [M]
-  const uint32_t* pairs;    // [P] i | (j << 16)
+  const float* sphere_off;  // [M] distance of the centre from its link's bounding-sphere centre
+  const float4* link_bs;    // [dof] bounding sphere of each link's spheres (link frame centre,
+                            //       radius; radius < 0 when the link has no enabled sphere)
+  const uint32_t* pairs;    // [P] i | (j << 16), grouped by link pair
+  const int* pair_orig;     // [P] position of each pair in the caller's list (ties: first wins)
+  const int4* groups;       // [G] (link a, link b, first pair, pair count)
 };
 
 // One box packed as four float4 rows: (R^T row k, t_k) for k = 0..2 so that
@@ -68,11 +74,11 @@ struct EvalArgs {
 
 // Shared-memory carve-up of the evaluation kernel (host and device agree).
 struct EvalSmem {
-  int off_fix, off_lim, off_sph, off_link, off_pairs, off_th, off_lt, off_sg, off_stw, off_sts,
-      off_sta, off_gth, off_wsph, off_box, off_sten, off_pb, off_db, off_sm, off_goal, off_free,
-      bytes;
+  int off_fix, off_lim, off_sph, off_link, off_soff, off_lbs, off_pairs, off_grp, off_th, off_lt,
+      off_sg, off_rho, off_stw, off_sts, off_sta, off_gth, off_wsph, off_wlc, off_surv, off_box,
+      off_sten, off_pb, off_db, off_sm, off_goal, off_free, bytes;
   __host__ __device__ static int align16(int x) { return (x + 15) & ~15; }
-  __host__ __device__ void build(int dof, int M, int P, int max_traj, int max_states,
+  __host__ __device__ void build(int dof, int M, int P, int G, int max_traj, int max_states,
                                  int max_horizon, int n_warps) {
     int o = 0;
     auto take = [&](int nbytes) { int r = o; o = align16(o + nbytes); return r; };
@@ -80,17 +86,25 @@ struct EvalSmem {
     off_lim = take(5 * dof * 4);
     off_sph = take(M * 16);
     off_link = take(M * 4);
+    off_soff = take(M * 4);
+    off_lbs = take(dof * 16);
     off_pairs = take(P * 4);
+    off_grp = take(G * 16);
     off_th = take(max_states * dof * 4);
     off_lt = take((1 + max_states) * dof * 12 * 4);
     off_sg = take(max_states * M * 16);
+    off_rho = take(max_states * dof * 16);
     off_stw = take(max_states * 4);
     off_sts = take(max_states * 4);
     off_sta = take(max_states * 4);
     off_gth = take(max_states * dof * 4);
     off_wsph = take(n_warps * M * 16);
+    off_wlc = take(n_warps * dof * 16);
+    off_surv = take(n_warps * kSurvivors * 4);
     off_box = take(kBoxChunk * 64);
-    int n_samples = max_traj * (max_horizon + 1) * dof;
+    // stencil samples of a tile: nt (H + 1) <= max_states + max_traj
+    int n_samples = (max_states + max_traj) * dof;
+    (void)max_horizon;
     off_sten = take(n_samples * 3 * 4);
     off_pb = take(max_states * dof * 4);
     off_db = take(n_samples * 4);
@@ -122,6 +136,7 @@ cudaError_t launch_fk(const RobotView& rb, const float* theta, int n, float* sph
 cudaError_t launch_eval(const EvalArgs& a, int grid, int block, cudaStream_t stream);
 int eval_smem_bytes(const EvalArgs& a, int block);
 int eval_blocks_per_sm(const EvalArgs& a, int block);
+int eval_smem_limit();  // largest dynamic shared memory a tile may use
 cudaError_t launch_opt(const OptArgs& a, int n_max, cudaStream_t stream);
 int opt_smem_bytes(int history, int n_max);
 

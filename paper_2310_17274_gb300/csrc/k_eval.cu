@@ -191,21 +191,28 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
   const float e2 = prm.eta_bound, inv_e2 = 1.f / prm.eta_bound;
   const float dt = prm.dt, inv2dt = 0.5f / dt;
 
+  const int G = a.rb.n_groups;
   EvalSmem L;
-  L.build(D, M, P, a.max_traj, a.max_states, a.max_horizon, nw);
+  L.build(D, M, P, G, a.max_traj, a.max_states, a.max_horizon, nw);
   float* s_fix = reinterpret_cast<float*>(smem + L.off_fix);
   float* s_lim = reinterpret_cast<float*>(smem + L.off_lim);
   float4* s_sph = reinterpret_cast<float4*>(smem + L.off_sph);
   int* s_link = reinterpret_cast<int*>(smem + L.off_link);
+  float* s_soff = reinterpret_cast<float*>(smem + L.off_soff);
+  float4* s_lbs = reinterpret_cast<float4*>(smem + L.off_lbs);
   uint32_t* s_pairs = reinterpret_cast<uint32_t*>(smem + L.off_pairs);
+  int4* s_grp = reinterpret_cast<int4*>(smem + L.off_grp);
   float* s_th = reinterpret_cast<float*>(smem + L.off_th);
   float* s_lt = reinterpret_cast<float*>(smem + L.off_lt);
   float4* s_sg = reinterpret_cast<float4*>(smem + L.off_sg);
+  float4* s_rho = reinterpret_cast<float4*>(smem + L.off_rho);
   float* s_stw = reinterpret_cast<float*>(smem + L.off_stw);
   float* s_sts = reinterpret_cast<float*>(smem + L.off_sts);
   int* s_sta = reinterpret_cast<int*>(smem + L.off_sta);
   float* s_gth = reinterpret_cast<float*>(smem + L.off_gth);
   float4* s_wsph = reinterpret_cast<float4*>(smem + L.off_wsph);
+  float4* s_wlc = reinterpret_cast<float4*>(smem + L.off_wlc);
+  int* s_surv = reinterpret_cast<int*>(smem + L.off_surv);
   BoxRows* s_box = reinterpret_cast<BoxRows*>(smem + L.off_box);
   float* s_sten = reinterpret_cast<float*>(smem + L.off_sten);
   float* s_pb = reinterpret_cast<float*>(smem + L.off_pb);
@@ -220,8 +227,11 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
   for (int k = tid; k < M; k += nthr) {
     s_sph[k] = a.rb.spheres[k];
     s_link[k] = a.rb.sphere_link[k];
+    s_soff[k] = a.rb.sphere_off[k];
   }
+  for (int k = tid; k < D; k += nthr) s_lbs[k] = a.rb.link_bs[k];
   for (int k = tid; k < P; k += nthr) s_pairs[k] = a.rb.pairs[k];
+  for (int k = tid; k < G; k += nthr) s_grp[k] = a.rb.groups[k];
   for (int k = tid; k < D; k += nthr) s_axis[k] = a.rb.axis[k];
 
   const int n_tiles = a.problems ? a.n_tiles
@@ -274,6 +284,7 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
       const float* q = s == 0 ? s_prob.q_start : s_th + (s - 1) * D;
       fk_chain(s_fix, s_axis, D, q, s_lt + s * D * 12);
     }
+    __syncthreads();
 
     // slot of timestep tt (0 = start, clamped to H) of trajectory r
     auto slot = [&](int r, int tt) -> int {
@@ -286,7 +297,60 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
       return tf_point(s_lt + (sl * D + s_link[i]) * 12, c.x, c.y, c.z);
     };
 
-    // ---- world term (Eq. 11 with the sweep of Sec. 3.4), box chunk by box chunk
+    // Neighbour positions of sphere i at state (r, t) for the sweep: the
+    // half distances L0, L2 to the previous / next waypoint and the unit
+    // directions.  thr = r + max(eta, L0, L2): a box farther than thr from
+    // the centre can add nothing (waypoint outside eta, no sweep sample
+    // reaches it) and is clear.
+    struct SphereMotion {
+      V3 x1, dir0, dir2;
+      float L0, L2, thr;
+    };
+    auto motion = [&](int r, int t, int i) -> SphereMotion {
+      SphereMotion mo;
+      mo.x1 = sphere_at(slot(r, t), i);
+      mo.dir0 = v3(0.f, 0.f, 0.f);
+      mo.dir2 = mo.dir0;
+      mo.L0 = 0.f;
+      mo.L2 = 0.f;
+      if (swept) {
+        const V3 d0 = sphere_at(slot(r, t - 1), i) - mo.x1;
+        const V3 d2 = sphere_at(slot(r, t + 1), i) - mo.x1;
+        const float n0 = norm(d0), n2 = norm(d2);
+        mo.L0 = 0.5f * n0;
+        mo.L2 = 0.5f * n2;
+        if (n0 > 0.f) mo.dir0 = (1.f / n0) * d0;
+        if (n2 > 0.f) mo.dir2 = (1.f / n2) * d2;
+      }
+      mo.thr = s_sph[i].w + fmaxf(eta, fmaxf(mo.L0, mo.L2));
+      return mo;
+    };
+
+    // ---- world term (Eq. 11 with the sweep of Sec. 3.4)
+    // (1) per state and link: link bounding-sphere centre and reach
+    //     rho_l = max over its spheres of (offset + thr): a box whose distance
+    //     to the centre is at least rho_l cannot touch any sphere of the link.
+    for (int sg = warp; sg < S; sg += nw) {
+      const int r = sg / H, t = sg % H + 1;
+      float4* rho = s_rho + sg * D;
+      if (lane < D) {
+        const float4 lb = s_lbs[lane];
+        const V3 c = tf_point(s_lt + (slot(r, t) * D + lane) * 12, lb.x, lb.y, lb.z);
+        rho[lane] = make_float4(c.x, c.y, c.z, __int_as_float(0xff800000));  // -inf
+      }
+      __syncwarp();
+      if (K > 0) {
+        for (int i = lane; i < M; i += 32) {
+          if (s_sph[i].w < 0.f) continue;
+          const SphereMotion mo = motion(r, t, i);
+          atomicMax(reinterpret_cast<int*>(&rho[s_link[i]].w), __float_as_int(s_soff[i] + mo.thr));
+        }
+      }
+      __syncwarp();
+    }
+    // (2) box chunk by box chunk: lanes test (link, box) pairs against the
+    //     reach; surviving pairs, in (link, box) order, send the link's
+    //     spheres through the per-sphere test and, when near, the sweep.
     for (int c0 = 0; c0 < K; c0 += kBoxChunk) {
       const int kc = min(kBoxChunk, K - c0);
       __syncthreads();
@@ -296,111 +360,163 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
         for (int k = tid; k < kc * 4; k += nthr) dst[k] = src[k];
       }
       __syncthreads();
+      int* surv = s_surv + warp * kSurvivors;
       for (int sg = warp; sg < S; sg += nw) {
         const int r = sg / H, t = sg % H + 1;
-        for (int i = lane; i < M; i += 32) {
-          const float rad = s_sph[i].w;
-          if (rad < 0.f) continue;
-          const V3 x1 = sphere_at(slot(r, t), i);
-          V3 dir0 = v3(0.f, 0.f, 0.f), dir2 = dir0;
-          float L0 = 0.f, L2 = 0.f;
-          if (swept) {
-            V3 d0 = sphere_at(slot(r, t - 1), i) - x1;
-            V3 d2 = sphere_at(slot(r, t + 1), i) - x1;
-            float n0 = norm(d0), n2 = norm(d2);
-            L0 = 0.5f * n0;
-            L2 = 0.5f * n2;
-            if (n0 > 0.f) dir0 = (1.f / n0) * d0;
-            if (n2 > 0.f) dir2 = (1.f / n2) * d2;
-          }
-          const float rhat = rad + eta;
-          // beyond this clearance neither the waypoint nor a sweep sample can
-          // reach the box: phi >= r + max(eta, L) adds exactly nothing
-          const float thr = rad + fmaxf(eta, fmaxf(L0, L2));
-          const float thr2 = thr * thr;
-          float4 acc4 = s_sg[sg * M + i];
-          bool clear = true;
-          for (int kk = 0; kk < kc; ++kk) {
-            const BoxRows b = s_box[kk];
-            const float ux = fmaf(b.r0.x, x1.x, fmaf(b.r0.y, x1.y, fmaf(b.r0.z, x1.z, b.r0.w)));
-            const float uy = fmaf(b.r1.x, x1.x, fmaf(b.r1.y, x1.y, fmaf(b.r1.z, x1.z, b.r1.w)));
-            const float uz = fmaf(b.r2.x, x1.x, fmaf(b.r2.y, x1.y, fmaf(b.r2.z, x1.z, b.r2.w)));
-            const float mx = fmaxf(fabsf(ux) - b.h.x, 0.f);
-            const float my = fmaxf(fabsf(uy) - b.h.y, 0.f);
-            const float mz = fmaxf(fabsf(uz) - b.h.z, 0.f);
-            if (fmaf(mx, mx, fmaf(my, my, mz * mz)) >= thr2) continue;
-            // slow path: waypoint, then the two half-way sweeps
-            SweepAcc sw{0.f, v3(0.f, 0.f, 0.f)};
-            bool hit;
-            const float phi1 = sample_pen(b, ux, uy, uz, rad, eta, inv_eta, sw, hit);
-            if (!(phi1 - rad > 0.f)) clear = false;
-            const float u0 = hit ? rhat : phi1 - rad;
-            if (swept) {
-#pragma unroll
-              for (int side = 0; side < 2; ++side) {
-                const float Ls = side == 0 ? L0 : L2;
-                if (!(Ls > 0.f)) continue;
-                const V3 dw = side == 0 ? dir0 : dir2;
-                // direction in the box frame (rotation only)
-                const float dx = fmaf(b.r0.x, dw.x, fmaf(b.r0.y, dw.y, b.r0.z * dw.z));
-                const float dy = fmaf(b.r1.x, dw.x, fmaf(b.r1.y, dw.y, b.r1.z * dw.z));
-                const float dz = fmaf(b.r2.x, dw.x, fmaf(b.r2.y, dw.y, b.r2.z * dw.z));
-                float u = u0;
-                for (int st = 0; st < prm.sweep_steps; ++st) {
-                  if (u >= Ls) break;
-                  const float phi = sample_pen(b, fmaf(u, dx, ux), fmaf(u, dy, uy), fmaf(u, dz, uz),
-                                               rad, eta, inv_eta, sw, hit);
-                  u += hit ? rhat : phi - rad;
-                }
+        const float4* rho = s_rho + sg * D;
+        const int n_lk = D * kc;
+        for (int p0 = 0; p0 < n_lk;) {
+          // list up to kSurvivors surviving (link, box) pairs starting at p0
+          int n_s = 0, p = p0;
+          for (; p < n_lk && n_s <= kSurvivors - 32; p += 32) {
+            const int q = p + lane;
+            bool keep = false;
+            if (q < n_lk) {
+              const int l = q / kc, kk = q % kc;
+              const float4 lc = rho[l];
+              if (lc.w >= 0.f) {
+                const BoxRows& b = s_box[kk];
+                const float ux = fmaf(b.r0.x, lc.x, fmaf(b.r0.y, lc.y, fmaf(b.r0.z, lc.z, b.r0.w)));
+                const float uy = fmaf(b.r1.x, lc.x, fmaf(b.r1.y, lc.y, fmaf(b.r1.z, lc.z, b.r1.w)));
+                const float uz = fmaf(b.r2.x, lc.x, fmaf(b.r2.y, lc.y, fmaf(b.r2.z, lc.z, b.r2.w)));
+                const float mx = fmaxf(fabsf(ux) - b.h.x, 0.f);
+                const float my = fmaxf(fabsf(uy) - b.h.y, 0.f);
+                const float mz = fmaxf(fabsf(uz) - b.h.z, 0.f);
+                keep = fmaf(mx, mx, fmaf(my, my, mz * mz)) < lc.w * lc.w;
               }
             }
-            // box frame -> world frame: grad_x = R grad_u, R = (R^T)^T
-            acc4.x += sw.S;
-            acc4.y += fmaf(b.r0.x, sw.g.x, fmaf(b.r1.x, sw.g.y, b.r2.x * sw.g.z));
-            acc4.z += fmaf(b.r0.y, sw.g.x, fmaf(b.r1.y, sw.g.y, b.r2.y * sw.g.z));
-            acc4.w += fmaf(b.r0.z, sw.g.x, fmaf(b.r1.z, sw.g.y, b.r2.z * sw.g.z));
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) surv[n_s + __popc(bal & ((1u << lane) - 1u))] = q;
+            n_s += __popc(bal);
           }
-          s_sg[sg * M + i] = acc4;
-          if (!clear) s_free[r] = 0;
+          p0 = p;
+          __syncwarp();
+          for (int u = 0; u < n_s; ++u) {
+            const int q = surv[u];
+            const int l = q / kc, kk = q % kc;
+            const BoxRows b = s_box[kk];
+            for (int i = lane; i < M; i += 32) {
+              const float rad = s_sph[i].w;
+              if (s_link[i] != l || rad < 0.f) continue;
+              const SphereMotion mo = motion(r, t, i);
+              const V3 x1 = mo.x1;
+              const float ux = fmaf(b.r0.x, x1.x, fmaf(b.r0.y, x1.y, fmaf(b.r0.z, x1.z, b.r0.w)));
+              const float uy = fmaf(b.r1.x, x1.x, fmaf(b.r1.y, x1.y, fmaf(b.r1.z, x1.z, b.r1.w)));
+              const float uz = fmaf(b.r2.x, x1.x, fmaf(b.r2.y, x1.y, fmaf(b.r2.z, x1.z, b.r2.w)));
+              const float mx = fmaxf(fabsf(ux) - b.h.x, 0.f);
+              const float my = fmaxf(fabsf(uy) - b.h.y, 0.f);
+              const float mz = fmaxf(fabsf(uz) - b.h.z, 0.f);
+              if (fmaf(mx, mx, fmaf(my, my, mz * mz)) >= mo.thr * mo.thr) continue;
+              // waypoint, then the two half-way sweeps
+              SweepAcc sw{0.f, v3(0.f, 0.f, 0.f)};
+              bool hit;
+              const float phi1 = sample_pen(b, ux, uy, uz, rad, eta, inv_eta, sw, hit);
+              if (!(phi1 - rad > 0.f)) s_free[r] = 0;
+              const float u0 = hit ? rad + eta : phi1 - rad;
+              if (swept) {
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                  const float Ls = side == 0 ? mo.L0 : mo.L2;
+                  if (!(Ls > 0.f)) continue;
+                  const V3 dw = side == 0 ? mo.dir0 : mo.dir2;
+                  // direction in the box frame (rotation only)
+                  const float dx = fmaf(b.r0.x, dw.x, fmaf(b.r0.y, dw.y, b.r0.z * dw.z));
+                  const float dy = fmaf(b.r1.x, dw.x, fmaf(b.r1.y, dw.y, b.r1.z * dw.z));
+                  const float dz = fmaf(b.r2.x, dw.x, fmaf(b.r2.y, dw.y, b.r2.z * dw.z));
+                  float u = u0;
+                  for (int st = 0; st < prm.sweep_steps; ++st) {
+                    if (u >= Ls) break;
+                    const float phi = sample_pen(b, fmaf(u, dx, ux), fmaf(u, dy, uy), fmaf(u, dz, uz),
+                                                 rad, eta, inv_eta, sw, hit);
+                    u += hit ? rad + eta : phi - rad;
+                  }
+                }
+              }
+              // box frame -> world frame: grad_x = R grad_u, R = (R^T)^T
+              float4 acc4 = s_sg[sg * M + i];
+              acc4.x += sw.S;
+              acc4.y += fmaf(b.r0.x, sw.g.x, fmaf(b.r1.x, sw.g.y, b.r2.x * sw.g.z));
+              acc4.z += fmaf(b.r0.y, sw.g.x, fmaf(b.r1.y, sw.g.y, b.r2.y * sw.g.z));
+              acc4.w += fmaf(b.r0.z, sw.g.x, fmaf(b.r1.z, sw.g.y, b.r2.z * sw.g.z));
+              s_sg[sg * M + i] = acc4;
+            }
+          }
+          __syncwarp();
         }
       }
     }
 
-    // ---- self-collision (Eq. 9): largest penetration over the pair set per state
+    // ---- self-collision (Eq. 9): largest penetration over the pair set per
+    // state; link pairs whose bounding spheres are 1 mm apart are skipped
     for (int sg = warp; sg < S; sg += nw) {
       const int r = sg / H, t = sg % H + 1;
       float4* wsp = s_wsph + warp * M;
+      float4* wlc = s_wlc + warp * D;
       for (int i = lane; i < M; i += 32) {
         V3 x = sphere_at(slot(r, t), i);
         wsp[i] = make_float4(x.x, x.y, x.z, s_sph[i].w);
       }
+      if (lane < D) {
+        const float4 lb = s_lbs[lane];
+        const V3 c = tf_point(s_lt + (slot(r, t) * D + lane) * 12, lb.x, lb.y, lb.z);
+        wlc[lane] = make_float4(c.x, c.y, c.z, lb.w);
+      }
       __syncwarp();
       float best = 0.f;
-      int arg = -1;
+      int arg = -1, arg_orig = 0x7fffffff;
       bool touch = false;
-      for (int p = lane; p < P; p += 32) {
-        const uint32_t pr = s_pairs[p];
-        const float4 A = wsp[pr & 0xffffu], B = wsp[pr >> 16];
-        if (A.w <= 0.f || B.w <= 0.f) continue;
-        const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
-        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float rs = A.w + B.w;
-        const float lim = rs + 1e-3f;
-        if (d2 >= lim * lim) continue;  // separated by more than 1 mm: no effect
-        const float pen = rs - sqrtf(d2);
-        if (!(-pen > 0.f)) touch = true;
-        if (pen > best) {  // lanes visit pairs in increasing order: ties keep the first
-          best = pen;
-          arg = p;
+      for (int g0 = 0; g0 < G; g0 += 32) {
+        bool near = false;
+        int4 gr = make_int4(0, 0, 0, 0);
+        if (g0 + lane < G) {
+          gr = s_grp[g0 + lane];
+          const float4 A = wlc[gr.x], B = wlc[gr.y];
+          if (A.w >= 0.f && B.w >= 0.f) {
+            const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
+            const float lim = A.w + B.w + 1e-3f;
+            near = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < lim * lim;
+          }
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, near);
+        while (bal) {
+          const int src = __ffs(bal) - 1;
+          bal &= bal - 1u;
+          const int first = __shfl_sync(0xffffffffu, gr.z, src);
+          const int count = __shfl_sync(0xffffffffu, gr.w, src);
+          for (int p = first + lane; p < first + count; p += 32) {
+            const uint32_t pr = s_pairs[p];
+            const float4 A = wsp[pr & 0xffffu], B = wsp[pr >> 16];
+            if (A.w <= 0.f || B.w <= 0.f) continue;
+            const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float rs = A.w + B.w;
+            const float lim = rs + 1e-3f;
+            if (d2 >= lim * lim) continue;  // separated by more than 1 mm: no effect
+            const float pen = rs - sqrtf(d2);
+            if (!(-pen > 0.f)) touch = true;
+            if (pen > best) {
+              best = pen;
+              arg = p;
+              arg_orig = a.rb.pair_orig[p];
+            } else if (pen == best && pen > 0.f) {  // exact tie: first in the caller's list
+              const int o = a.rb.pair_orig[p];
+              if (o < arg_orig) {
+                arg = p;
+                arg_orig = o;
+              }
+            }
+          }
         }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oa = __shfl_xor_sync(0xffffffffu, arg, o);
-        if (ob > best || (ob == best && ob > 0.f && oa < arg)) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+        const int oo = __shfl_xor_sync(0xffffffffu, arg_orig, o);
+        if (ob > best || (ob == best && ob > 0.f && oo < arg_orig)) {
           best = ob;
           arg = oa;
+          arg_orig = oo;
         }
       }
       touch = __any_sync(0xffffffffu, touch);
@@ -693,9 +809,9 @@ __global__ void k_fk(RobotView rb, const float* __restrict__ theta, int n, float
 
 }  // namespace
 
-// The largest dynamic shared memory any launch may ask for (227 KB) is set
-// once per kernel and device, never lowered, so launches captured in a graph
-// stay valid whatever is launched later.
+// The largest dynamic shared memory any launch may ask for (the opt-in
+// limit) is set once per kernel and device, never lowered, so launches
+// captured in a graph stay valid whatever is launched later.
 template <int DMAX>
 cudaError_t allow_eval_smem() {
   static unsigned done = 0;  // bit per device
@@ -703,9 +819,24 @@ cudaError_t allow_eval_smem() {
   cudaGetDevice(&dev);
   const unsigned bit = 1u << (dev & 31);
   if (done & bit) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_eval<DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  // opt-in limit minus the kernel's static shared memory
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, k_eval<DMAX>);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_eval<DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes);
   if (e == cudaSuccess) done |= bit;
   return e;
+}
+
+int eval_smem_limit() {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return optin - 1024;  // room for the kernel's static shared memory
 }
 
 int eval_blocks_per_sm(const EvalArgs& a, int block) {
@@ -723,8 +854,8 @@ int eval_blocks_per_sm(const EvalArgs& a, int block) {
 
 int eval_smem_bytes(const EvalArgs& a, int block) {
   EvalSmem L;
-  L.build(a.rb.dof, a.rb.n_spheres, a.rb.n_pairs, a.max_traj, a.max_states, a.max_horizon,
-          block / 32);
+  L.build(a.rb.dof, a.rb.n_spheres, a.rb.n_pairs, a.rb.n_groups, a.max_traj, a.max_states,
+          a.max_horizon, block / 32);
   return L.bytes;
 }
 

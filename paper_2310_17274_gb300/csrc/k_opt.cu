@@ -338,6 +338,8 @@ cudaError_t allow_opt_smem() {
   cudaGetDevice(&dev);
   const unsigned bit = 1u << (dev & 31);
   if (done & bit) return cudaSuccess;
+  // 200 KB covers every accepted history * horizon * dof and stays below the
+  // opt-in limit together with the kernel's static shared memory
   cudaError_t e = cudaFuncSetAttribute(k_opt<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess) done |= bit;
   return e;

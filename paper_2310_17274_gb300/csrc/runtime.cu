@@ -304,7 +304,7 @@ cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* p
     EvalArgs a = eval_args(cand);
     const int block = ctx->block;
     const int smem = eval_smem_bytes(a, block);
-    if (smem > 227 * 1024) return failf(CR_EINVAL, "tile needs %d bytes of shared memory", smem);
+    if (smem > eval_smem_limit()) return failf(CR_EINVAL, "tile needs %d bytes of shared memory", smem);
     int grid = a.n_tiles;
     if (persistent) {
       const int per_sm = std::max(1, eval_blocks_per_sm(a, block));
