@@ -249,6 +249,38 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
                    const cr_params* params, int32_t iters, uint32_t solve_flags,
                    const cr_result* results, void* stream);
 
+/* ------------------------------------------------------------------------- */
+/* Evaluation without allocation                                              */
+/* ------------------------------------------------------------------------- */
+#define CR_NOALLOC_MAX_PROBLEMS 256
+#define CR_NOALLOC_MAX_TILES 32768
+
+/* The paper has no counterpart to this entry point.  It serves callers that
+ * cannot let a library allocate device memory: a controller's real-time loop
+ * that must not call cudaMalloc/cudaFree once running (those calls can take
+ * unbounded time and synchronise the device), or an application whose own
+ * pool owns all device memory.  It evaluates cost, gradient, flags and terms
+ * (as cr_eval) of the trajectories of n_problems problems in one persistent
+ * launch and allocates nothing: its scratch (problem and tile tables and a
+ * work counter) is one fixed device array of about 0.6 MB inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   n_traj  host [n_problems]: trajectories of each problem (problems[p].seeds
+ *           and n_seeds are unused)
+ *   theta   device: each problem's block [n_traj[p]][H_p][dof], problem
+ *           after problem
+ *   cost, cfree, terms  device, per trajectory in the same order; grad like theta
+ * At most CR_NOALLOC_MAX_PROBLEMS problems and CR_NOALLOC_MAX_TILES tiles (one
+ * tile per trajectory when H >= 32, ceil(32/H) trajectories per tile below);
+ * larger batches return CR_EINVAL.  The first call on a device looks up the
+ * array's device address (a one-time set-up with that device current); make
+ * that first call before any stream capture.  Every call shares the one
+ * array, so calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race: order them on one stream.  Results equal
+ * those of cr_eval on each problem. */
+cr_status cr_eval_batch_noalloc(const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
+                                const cr_params* params, const int32_t* n_traj, const float* theta,
+                                float* cost, float* grad, uint8_t* cfree, float* terms, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,8 @@ SIGNATURES = {
     "cr_context_destroy": ([_vp], None),
     "cr_solve": ([_vp, _vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), C.c_int32, C.c_uint32,
                   C.POINTER(Result), _vp], C.c_int32),
+    "cr_eval_batch_noalloc": ([_vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), _ip, _vp, _vp,
+                               _vp, _vp, _vp, _vp], C.c_int32),
 }
 
 
@@ -377,3 +379,35 @@ def solve(ctx: Context, robot: Robot, problems, params=None, iters=25, graph=Tru
     check(lib().cr_solve(ctx.handle, robot.handle, n, arr, C.byref(P), int(iters), flags, res,
                          _stream(stream)), "cr_solve")
     return outputs
+
+
+def evaluate_batch_noalloc(robot: Robot, problems, thetas, params=None, stream=None):
+    """Evaluate several problems' trajectories in one launch through the entry
+    point that allocates nothing on the device (the caller passes every input
+    and output buffer).  thetas: one CUDA tensor [n_traj, H, dof] per problem.
+    Returns per-problem dicts of cost / grad / cfree / terms (views into
+    concatenated output tensors)."""
+    import torch
+    probs = list(problems)
+    n = len(probs)
+    arr = (Problem * n)(*[p.struct() for p in probs])
+    counts = _i32([int(t.shape[0]) for t in thetas])
+    theta = torch.cat([t.contiguous().view(-1) for t in thetas]).contiguous()
+    T = int(counts.sum())
+    dev = theta.device
+    cost = torch.empty(T, device=dev)
+    grad = torch.empty_like(theta)
+    cfree = torch.empty(T, device=dev, dtype=torch.uint8)
+    terms = torch.empty((T, N_TERMS), device=dev)
+    P = params if isinstance(params, Params) else make_params(params)
+    check(lib().cr_eval_batch_noalloc(robot.handle, n, arr, C.byref(P), _p(counts, _ip), _dptr(theta),
+                                      _dptr(cost), _dptr(grad), _dptr(cfree), _dptr(terms),
+                                      _stream(stream)), "cr_eval_batch_noalloc")
+    out, t0, v0 = [], 0, 0
+    for t in thetas:
+        nt, nv = int(t.shape[0]), t.numel()
+        out.append(dict(cost=cost[t0:t0 + nt], grad=grad[v0:v0 + nv].view(t.shape),
+                        cfree=cfree[t0:t0 + nt], terms=terms[t0:t0 + nt]))
+        t0 += nt
+        v0 += nv
+    return out
