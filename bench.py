@@ -38,6 +38,24 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float) -> float:
+    """Largest value over the ranks of the process group (itself alone when
+    there is none): the whole job ends when its slowest replica does."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, steps: int, world_size: int, t_max: float) -> float:
+    """Units of all replicas divided by the slowest replica's time."""
+    return units_per_rank * steps * world_size / t_max
+
+
 # ---------------------------------------------------------------------------
 # workload (synthetic, seeded)
 # ---------------------------------------------------------------------------
@@ -228,7 +246,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="crgb")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="ik,uneven,plain")
+    ap.add_argument("--extras", default="ik,uneven,plain,serve")
+    ap.add_argument("--serve-rate", type=float, default=500.0)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--profile", type=int, default=0,
                     help="only run N fused evaluations of one line-search batch inside the NVTX "
                          "range crgb_eval (for ncu), then exit")
@@ -301,12 +321,8 @@ def main():
             torch.cuda.synchronize()
             times.append(ev0.elapsed_time(ev1) / 1e3)
     clocks = clk.summary()
-    t_total = float(np.sum(times))
-    if ws > 1:
-        t = torch.tensor([t_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-    value = units * args.steps * ws / t_total
+    t_total = max_over_ranks(float(np.sum(times)))
+    value = whole_job_rate(units, args.steps, ws, t_total)
     launches_per_step = 2 + 2 * iters + 1
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
@@ -327,12 +343,8 @@ def main():
         torch.cuda.synchronize()
         if k >= args.warmup:
             e2e_times.append(time.perf_counter() - t0)
-    t_e2e = float(np.sum(e2e_times))
-    if ws > 1:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e_value = units * args.steps * ws / t_e2e
+    t_e2e = max_over_ranks(float(np.sum(e2e_times)))
+    e2e_value = whole_job_rate(units, args.steps, ws, t_e2e)
     h2d = pr.seeds.size * 4
     d2h = h_traj.numel() * 4 + h_cost.numel() * 4 + h_free.numel() + h_best.numel() * 4
 
@@ -394,6 +406,10 @@ def main():
         extras["ik"] = bench_ik(crgb, synth, ctx, R, rb)
     if rank == 0 and "uneven" in want:
         extras["uneven"] = bench_uneven(crgb, synth, ctx, R, rb)
+    if rank == 0 and "serve" in want:
+        from paper_2310_17274_gb300 import serve
+        extras["serve"] = serve.serving_benchmark(crgb, synth, ctx, R, rb, rate=args.serve_rate,
+                                                  seconds=args.serve_seconds, plain_seconds=2.0)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -440,7 +456,16 @@ def bench_ik(crgb, synth, ctx, R, rb, n_goals=1000, n_seeds=32, iters=50):
 
     world = synth.make_world(cfg.n_boxes, cfg.world_seed, reject)
     W = crgb.World(world)
-    qg = synth.uniform_config(rng, rb, n_goals)
+    # reachable, collision-free goals: FK of configurations sampled within the
+    # limits, kept when the library's own check finds them free
+    probe = crgb.ProblemSpec(W, qs, np.array([0, 0, 0, 1.0, 0, 0, 0]), 1)
+    qg = np.zeros((0, rb.dof))
+    while len(qg) < n_goals:
+        cand = synth.uniform_config(rng, rb, 4096)
+        ev = crgb.evaluate(R, probe, torch.tensor(cand[:, None, :], dtype=torch.float32, device="cuda"),
+                           ikp, want_grad=False, want_terms=False)
+        qg = np.concatenate([qg, cand[ev["cfree"].cpu().numpy().astype(bool)]])
+    qg = qg[:n_goals]
     _, ee, _ = crgb.fk(R, torch.tensor(qg, dtype=torch.float32, device="cuda"), spheres=False)
     ee = ee.cpu().numpy().astype(np.float64).reshape(-1, 3, 4)
     goals = np.stack([np.concatenate([e[:, 3], _rot_to_quat(e[:, :3])]) for e in ee])
@@ -468,9 +493,15 @@ def bench_ik(crgb, synth, ctx, R, rb, n_goals=1000, n_seeds=32, iters=50):
     Rg = np.stack([_quat_rot(g[3:]) for g in goals])
     dq = (3 - np.einsum("nij,nij->n", Rg, eb[:, :, :3])) / 4
     solved = free & (pos_err <= 5e-3) & (dq <= 1e-3)
+    if os.environ.get("CRGB_BENCH_DEBUG"):
+        print("ik debug: free", free.mean(), "pos<5mm", (pos_err <= 5e-3).mean(), "dq<1e-3",
+              (dq <= 1e-3).mean(), "median pos", np.median(pos_err), "median dq", np.median(dq),
+              "median best cost", np.median([float(o.cost[int(o.best)]) for o in outs]), file=sys.stderr)
     return {"goals": n_goals, "seeds": n_seeds, "iters": iters, "ms_per_batch": t * 1e3,
-            "ik_solves_per_s": n_goals / t, "success_rate": float(solved.mean()),
-            "evals_per_s": n_goals * n_seeds * (iters * ikp.n_alpha + 1) / t}
+            "ik_goals_per_s": n_goals / t, "success_rate": float(solved.mean()),
+            "ik_solves_per_s": float(solved.sum()) / t,
+            "evals_per_s": n_goals * n_seeds * (iters * ikp.n_alpha + 1) / t,
+            "goals_from": "FK of collision-free configurations sampled within the limits"}
 
 
 def _quat_rot(q):

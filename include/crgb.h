@@ -249,6 +249,62 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
                    const cr_params* params, int32_t iters, uint32_t solve_flags,
                    const cr_result* results, void* stream);
 
+/* Autotuner: time cr_solve of this batch (`iters` iterations) for each tile
+ * shape -- CTA size 256 or 512 threads; when a horizon is below 32, 8, 16,
+ * 32 or 64 states per tile; sphere positions cached in shared memory or
+ * recomputed (a smaller tile, so more CTAs share an SM) -- and keep the
+ * fastest in the context for every problem shape of the batch (spheres, box
+ * count rounded up to a power of two, horizon); later cr_solve calls on those
+ * shapes use it.  Results do not depend on the tile shape.  Synchronous.
+ * Writes the choice and its time (any output may be NULL). */
+cr_status cr_autotune(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
+                      const cr_params* params, int32_t iters, int32_t* block, int32_t* short_tile,
+                      int32_t* no_cache, float* ms);
+/* Set the tile shape of one problem shape by hand (block 256 or 512;
+ * no_cache = 1 recomputes sphere positions instead of caching them). */
+cr_status cr_tune_set(cr_ctx* ctx, int32_t n_spheres, int32_t n_boxes, int32_t horizon, int32_t block,
+                      int32_t short_tile, int32_t no_cache);
+
+/* ------------------------------------------------------------------------- */
+/* Serving: continuous batching of motion-generation and IK requests          */
+/* ------------------------------------------------------------------------- */
+typedef struct cr_server cr_server;
+
+/* Request kinds: 0 = trajectory optimisation (motion generation), 1 = IK. */
+typedef struct {
+  int32_t kind_seeds[2];      /* seeds per request of each kind */
+  int32_t kind_horizon[2];    /* horizon per request (IK: 1) */
+  int32_t kind_iters[2];      /* L-BFGS iterations per request, multiples of chunk */
+  cr_params kind_params[2];   /* parameters per kind (IK: CR_IK_MODE) */
+  int32_t chunk;              /* iterations each step runs for every active request */
+  int32_t max_active;         /* cap on active requests per kind (0 = memory decides) */
+  size_t reserve_bytes;       /* free device memory never given to request state */
+} cr_server_config;
+
+/* A server keeps the optimiser state of every active request on the device
+ * (Sec. 4.1 state: iterate, gradient, history, candidates, best iterate). */
+cr_status cr_server_create(cr_ctx* ctx, const cr_robot* robot, const cr_server_config* cfg,
+                           cr_server** out);
+void cr_server_destroy(cr_server* server);
+/* Queue a request (host inputs copied; problem->seeds [B][H][dof] host).
+ * It is admitted by a later step once a slot and free device memory allow. */
+cr_status cr_server_submit(cr_server* server, int32_t kind, const cr_problem* problem,
+                           uint64_t* ticket);
+/* One step: admit queued requests while free memory minus the reserve allows
+ * (their initial evaluation and first L-BFGS step run), run `chunk`
+ * iterations for every active request (one evaluation launch per kind over
+ * all its requests' line-search candidates, one selection + L-BFGS launch;
+ * the two kinds on two streams), retire finished requests.  Blocks until
+ * the step's work is done.  Each request's result equals cr_solve of that
+ * request alone with its kind's parameters and iterations. */
+cr_status cr_server_step(cr_server* server, void* stream);
+/* Results of a finished request into host buffers (any may be NULL):
+ * traj [B][H][dof], cost [B], cfree [B], best seed index.  *done = 0 while pending. */
+cr_status cr_server_poll(cr_server* server, uint64_t ticket, int32_t* done, float* traj,
+                         float* cost, uint8_t* cfree, int32_t* best);
+/* Active and queued requests, device bytes held by request state. */
+cr_status cr_server_stats(cr_server* server, int32_t* active, int32_t* queued, size_t* pool_bytes);
+
 /* ------------------------------------------------------------------------- */
 /* Evaluation without allocation                                              */
 /* ------------------------------------------------------------------------- */

@@ -91,6 +91,19 @@ SIGNATURES = {
     "cr_context_destroy": ([_vp], None),
     "cr_solve": ([_vp, _vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), C.c_int32, C.c_uint32,
                   C.POINTER(Result), _vp], C.c_int32),
+    "cr_autotune": ([_vp, _vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), C.c_int32,
+                     C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                     C.POINTER(C.c_float)], C.c_int32),
+    "cr_tune_set": ([_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
+                    C.c_int32),
+    "cr_server_create": ([_vp, _vp, _vp, C.POINTER(_vp)], C.c_int32),
+    "cr_server_destroy": ([_vp], None),
+    "cr_server_submit": ([_vp, C.c_int32, C.POINTER(Problem), C.POINTER(C.c_uint64)], C.c_int32),
+    "cr_server_step": ([_vp, _vp], C.c_int32),
+    "cr_server_poll": ([_vp, C.c_uint64, C.POINTER(C.c_int32), _vp, _vp, _vp, C.POINTER(C.c_int32)],
+                       C.c_int32),
+    "cr_server_stats": ([_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_size_t)],
+                        C.c_int32),
     "cr_eval_batch_noalloc": ([_vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), _ip, _vp, _vp,
                                _vp, _vp, _vp, _vp], C.c_int32),
 }
@@ -411,3 +424,92 @@ def evaluate_batch_noalloc(robot: Robot, problems, thetas, params=None, stream=N
         t0 += nt
         v0 += nv
     return out
+
+
+def autotune(ctx: Context, robot: Robot, problems, params=None, iters=2):
+    """Measure the tile shapes on this batch and keep the fastest in ctx.
+    Returns dict(block, short_tile, ms)."""
+    probs = list(problems)
+    arr = (Problem * len(probs))(*[p.struct() for p in probs])
+    P = params if isinstance(params, Params) else make_params(params)
+    bl, sh, nc, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_float()
+    check(lib().cr_autotune(ctx.handle, robot.handle, len(probs), arr, C.byref(P), int(iters),
+                            C.byref(bl), C.byref(sh), C.byref(nc), C.byref(ms)), "cr_autotune")
+    return dict(block=bl.value, short_tile=sh.value, no_cache=nc.value, ms=ms.value)
+
+
+def tune_set(ctx: Context, n_spheres, n_boxes, horizon, block, short_tile, no_cache=0):
+    check(lib().cr_tune_set(ctx.handle, int(n_spheres), int(n_boxes), int(horizon), int(block),
+                            int(short_tile), int(no_cache)), "cr_tune_set")
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+
+class ServerConfig(C.Structure):
+    _fields_ = [("kind_seeds", C.c_int32 * 2), ("kind_horizon", C.c_int32 * 2),
+                ("kind_iters", C.c_int32 * 2), ("kind_params", Params * 2), ("chunk", C.c_int32),
+                ("max_active", C.c_int32), ("reserve_bytes", C.c_size_t)]
+
+
+MG, IK = 0, 1
+
+
+class Server:
+    """Continuous-batching server (cr_server_*): requests of two kinds, state
+    resident on the device, admission by free device memory."""
+
+    def __init__(self, ctx: Context, robot: Robot, mg=(32, 48, 100), ik=(32, 1, 50),
+                 mg_params=None, ik_params=None, chunk=10, max_active=0, reserve_bytes=2 << 30):
+        cfg = ServerConfig()
+        for k, (B, H, it) in enumerate((mg, ik)):
+            cfg.kind_seeds[k], cfg.kind_horizon[k], cfg.kind_iters[k] = B, H, it
+        cfg.kind_params[0] = mg_params if isinstance(mg_params, Params) else make_params(mg_params)
+        ikp = ik_params if ik_params is not None else dict(flags=IK_MODE | SELF | WOLFE)
+        cfg.kind_params[1] = ikp if isinstance(ikp, Params) else make_params(ikp)
+        cfg.chunk, cfg.max_active, cfg.reserve_bytes = chunk, max_active, reserve_bytes
+        self.shape = {MG: (mg[0], mg[1]), IK: (ik[0], ik[1])}
+        self.dof = robot.dof
+        h = _vp()
+        check(lib().cr_server_create(ctx.handle, robot.handle, C.byref(cfg), C.byref(h)),
+              "cr_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.cr_server_destroy(h)
+            self.handle = None
+
+    def submit(self, kind, spec: ProblemSpec) -> int:
+        pr = spec.struct()
+        t = C.c_uint64()
+        check(lib().cr_server_submit(self.handle, int(kind), C.byref(pr), C.byref(t)),
+              "cr_server_submit")
+        self._keep[t.value] = kind
+        return t.value
+
+    def step(self, stream=None):
+        check(lib().cr_server_step(self.handle, _stream(stream)), "cr_server_step")
+
+    def poll(self, ticket):
+        """None while pending, else dict(traj, cost, cfree, best) (host numpy)."""
+        kind = self._keep[ticket]
+        B, H = self.shape[kind]
+        done = C.c_int32()
+        traj = np.empty((B, H, self.dof), dtype=np.float32)
+        cost = np.empty(B, dtype=np.float32)
+        cfree = np.empty(B, dtype=np.uint8)
+        best = C.c_int32()
+        check(lib().cr_server_poll(self.handle, int(ticket), C.byref(done), _p(traj), _p(cost),
+                                   _p(cfree, _up), C.byref(best)), "cr_server_poll")
+        if not done.value:
+            return None
+        return dict(traj=traj, cost=cost, cfree=cfree.astype(bool), best=best.value)
+
+    def stats(self):
+        a, q, b = C.c_int32(), C.c_int32(), C.c_size_t()
+        check(lib().cr_server_stats(self.handle, C.byref(a), C.byref(q), C.byref(b)), "cr_server_stats")
+        return dict(active=a.value, queued=q.value, pool_bytes=b.value)

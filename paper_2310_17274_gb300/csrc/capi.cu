@@ -105,7 +105,7 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
   }
   // Bounding sphere of each link's enabled spheres (link frame): a lower
   // bound on every distance of the link's spheres, used to skip whole links.
-  std::vector<float> lbs((size_t)D * 4, 0.f), soff(M, 0.f);
+  std::vector<float> lbs((size_t)D * 4, 0.f), soff(M, 0.f), ldmax(D, 0.f);
   for (int l = 0; l < D; ++l) {
     double c[3] = {0, 0, 0};
     int cnt = 0;
@@ -124,6 +124,7 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
           double o = std::sqrt(dx * dx + dy * dy + dz * dz);
           soff[i] = (float)(o * (1.0 + 1e-6) + 1e-6);  // rounded up: stays a bound in FP32
           R = std::max(R, (double)soff[i] + d->spheres[4 * i + 3]);
+          ldmax[l] = std::max(ldmax[l], soff[i]);
         }
     }
     for (int a = 0; a < 3; ++a) lbs[4 * l + a] = (float)c[a];
@@ -157,7 +158,7 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
   auto take = [&](size_t bytes) { size_t r = off; off = (off + bytes + 255) & ~size_t(255); return r; };
   const size_t o_fix = take(n_fix * 4), o_lim = take(n_lim * 4), o_sph = take((size_t)M * 16),
                o_axis = take((size_t)D * 4), o_link = take((size_t)M * 4),
-               o_soff = take((size_t)M * 4), o_lbs = take((size_t)D * 16),
+               o_soff = take((size_t)M * 4), o_lbs = take((size_t)D * 16), o_ldm = take((size_t)D * 4),
                o_pairs = take((size_t)(P > 0 ? P : 1) * 4), o_orig = take((size_t)(P > 0 ? P : 1) * 4),
                o_grp = take((size_t)(G > 0 ? G : 1) * 16);
   std::vector<unsigned char> host(off, 0);
@@ -175,6 +176,7 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
   std::memcpy(host.data() + o_link, d->sphere_link, (size_t)M * 4);
   std::memcpy(host.data() + o_soff, soff.data(), (size_t)M * 4);
   std::memcpy(host.data() + o_lbs, lbs.data(), (size_t)D * 16);
+  std::memcpy(host.data() + o_ldm, ldmax.data(), (size_t)D * 4);
   if (P > 0) {
     std::memcpy(host.data() + o_pairs, pairs.data(), (size_t)P * 4);
     std::memcpy(host.data() + o_orig, orig.data(), (size_t)P * 4);
@@ -208,6 +210,7 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
   r->view.n_groups = G;
   r->view.sphere_off = reinterpret_cast<const float*>(b + o_soff);
   r->view.link_bs = reinterpret_cast<const float4*>(b + o_lbs);
+  r->view.link_dmax = reinterpret_cast<const float*>(b + o_ldm);
   for (int j = 0; j < D; ++j) {
     r->q_lo[j] = d->q_lo[j];
     r->q_hi[j] = d->q_hi[j];
@@ -352,7 +355,7 @@ cr_status cr_eval(const cr_robot* robot, const cr_problem* problem, const cr_par
   a.grad = grad;
   a.cfree = cfree;
   a.terms = terms;
-  const int block = 256;
+  const int block = kEvalBlock;
   const int smem = eval_smem_bytes(a, block);
   if (smem > eval_smem_limit())
     return fail(CR_EINVAL, "cr_eval: tile needs %d bytes of shared memory (> 227 KB)", smem);

@@ -15,7 +15,7 @@ constexpr int kMaxPairs = 65535;
 constexpr int kMaxBoxes = 4096;
 constexpr int kMaxHorizon = 128;
 constexpr int kBoxChunk = 64;  // boxes staged in shared memory at a time
-constexpr int kSurvivors = 64; // (link, box) pairs a warp lists per round
+constexpr int kEvalBlock = 512; // threads of an evaluation CTA
 
 // Robot as the kernels see it (device pointers into one allocation).
 struct RobotView {
@@ -28,6 +28,7 @@ struct RobotView {
   const float* sphere_off;  // [M] distance of the centre from its link's bounding-sphere centre
   const float4* link_bs;    // [dof] bounding sphere of each link's spheres (link frame centre,
                             //       radius; radius < 0 when the link has no enabled sphere)
+  const float* link_dmax;   // [dof] largest sphere_off of each link
   const uint32_t* pairs;    // [P] i | (j << 16), grouped by link pair
   const int* pair_orig;     // [P] position of each pair in the caller's list (ties: first wins)
   const int4* groups;       // [G] (link a, link b, first pair, pair count)
@@ -61,6 +62,8 @@ struct EvalArgs {
   const int4* tiles;             // batched launch: (problem, first traj, n traj, -)
   int n_tiles;
   int* queue;                    // persistent launch: work counter (zeroed before launch), or nullptr
+  int store_x;                   // set by the launcher: keep sphere positions in shared memory
+  int no_store_x;                // tile option: never keep them (smaller tiles, more CTAs per SM)
   int traj_per_tile;             // single-problem launch: trajectories per CTA
   int max_traj;                  // largest trajectory count of a tile
   int max_states;                // largest (trajectories x horizon) of a tile
@@ -73,13 +76,17 @@ struct EvalArgs {
 };
 
 // Shared-memory carve-up of the evaluation kernel (host and device agree).
+// With store_x the world positions of every sphere of every state of the
+// tile are kept (read by all later passes); without, they are recomputed
+// from the link transforms (long horizons that would not fit).
 struct EvalSmem {
-  int off_fix, off_lim, off_sph, off_link, off_soff, off_lbs, off_pairs, off_grp, off_th, off_lt,
-      off_sg, off_rho, off_stw, off_sts, off_sta, off_gth, off_wsph, off_wlc, off_surv, off_box,
-      off_sten, off_pb, off_db, off_sm, off_goal, off_free, bytes;
+  int off_fix, off_lim, off_sph, off_link, off_soff, off_lbs, off_ldm, off_pairs, off_grp, off_th,
+      off_lt, off_sc, off_x, off_sg, off_nz, off_rho, off_lm, off_mask, off_gmask, off_stw,
+      off_sts, off_sta, off_gth, off_wsph, off_box, off_ee, off_sten, off_pb, off_db, off_sm, off_goal,
+      off_free, bytes;
   __host__ __device__ static int align16(int x) { return (x + 15) & ~15; }
   __host__ __device__ void build(int dof, int M, int P, int G, int max_traj, int max_states,
-                                 int max_horizon, int n_warps) {
+                                 int n_warps, bool store_x) {
     int o = 0;
     auto take = [&](int nbytes) { int r = o; o = align16(o + nbytes); return r; };
     off_fix = take((dof + 1) * 12 * 4);
@@ -88,23 +95,28 @@ struct EvalSmem {
     off_link = take(M * 4);
     off_soff = take(M * 4);
     off_lbs = take(dof * 16);
+    off_ldm = take(dof * 4);
     off_pairs = take(P * 4);
     off_grp = take(G * 16);
     off_th = take(max_states * dof * 4);
     off_lt = take((1 + max_states) * dof * 12 * 4);
+    off_sc = take((1 + max_states) * dof * 8);
+    off_x = take(store_x ? (1 + max_states) * M * 16 : 0);
     off_sg = take(max_states * M * 16);
+    off_nz = take(max_states * ((M + 31) / 32) * 4);
     off_rho = take(max_states * dof * 16);
+    off_lm = take(max_states * dof * 4);
+    off_mask = take(max_states * dof * 8);  // 64 box bits per (state, link)
+    off_gmask = take(max_states * ((G + 31) / 32) * 4);
     off_stw = take(max_states * 4);
     off_sts = take(max_states * 4);
     off_sta = take(max_states * 4);
     off_gth = take(max_states * dof * 4);
-    off_wsph = take(n_warps * M * 16);
-    off_wlc = take(n_warps * dof * 16);
-    off_surv = take(n_warps * kSurvivors * 4);
+    off_wsph = take(store_x ? 0 : n_warps * M * 16);
     off_box = take(kBoxChunk * 64);
+    off_ee = take(max_traj * 48);
     // stencil samples of a tile: nt (H + 1) <= max_states + max_traj
-    int n_samples = (max_states + max_traj) * dof;
-    (void)max_horizon;
+    const int n_samples = (max_states + max_traj) * dof;
     off_sten = take(n_samples * 3 * 4);
     off_pb = take(max_states * dof * 4);
     off_db = take(n_samples * 4);
@@ -123,14 +135,28 @@ struct OptArgs {
   int dof;
   int n_seeds;
   int horizon;         // uniform horizon (single problem), or 0 with seed table
-  const int4* seed_tab;  // batched: per seed (n vars, var offset, cand offset, problem), or nullptr
+  const int4* seed_tab;  // batched: per listed seed (n vars, var offset, seed index, problem), or nullptr
   cr_opt_state st;
   int do_select;
   int do_propose;
   int init_best;       // first call after the initial evaluation: best := current
+  int* reset_queue;    // the next evaluation's work counter, zeroed here (or nullptr)
 };
 
-// launch helpers (k_eval.cu / k_opt.cu)
+// Per-problem output pointers of the finishing kernel (runtime.cu).
+struct ResultView {
+  float* traj;
+  float* cost;
+  uint8_t* cfree;
+  int* best;
+  int n_seeds, n, seed_base, var_base;
+};
+
+// launch helpers (k_eval.cu / k_opt.cu / runtime.cu)
+cudaError_t launch_finish(const ResultView* res, int n_problems, const float* best_x,
+                          const float* best_c, const uint8_t* best_cfree, cudaStream_t s);
+cr_status check_params(const cr_params* p);
+cr_status fill_problem(const cr_robot* rb, const cr_problem* pr, ProblemView* pv);
 cudaError_t launch_fk(const RobotView& rb, const float* theta, int n, float* spheres, float* ee,
                       float* link_tf, cudaStream_t stream);
 cudaError_t launch_eval(const EvalArgs& a, int grid, int block, cudaStream_t stream);

@@ -50,12 +50,17 @@ __device__ __forceinline__ V3 tf_point(const float* T, float cx, float cy, float
 // the "full link transformation" of App. E.1's joint table (two columns of F
 // mixed by cos / sin).  Writes T_0..T_{dof-1} (12 floats each).
 __device__ __forceinline__ void fk_chain(const float* fix, const int* axis, int dof,
-                                         const float* q, float* out) {
+                                         const float* q, const float2* sc, float* out) {
   float T[12] = {1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f};
   for (int j = 0; j < dof; ++j) {
     const float* F = fix + 12 * j;
     float s, c;
-    sincosf(q[j], &s, &c);
+    if (sc) {
+      s = sc[j].x;
+      c = sc[j].y;
+    } else {
+      sincosf(q[j], &s, &c);
+    }
     float A[12];
     const int ax = axis[j];
 #pragma unroll
@@ -140,8 +145,15 @@ __device__ __forceinline__ float bound_cost(float q, float lo, float hi, float e
   return 0.f;
 }
 
+// log cosh x.  For |x| >= 1/8: |x| + log(1 + e^{-2|x|}) - log 2; below, where
+// that form cancels in FP32, the Taylor series x^2/2 - x^4/12 + x^6/45
+// (next term 17 x^8 / 2520, below 1e-7 relative there).
 __device__ __forceinline__ float logcoshf(float x) {
-  float a = fabsf(x);
+  const float a = fabsf(x);
+  if (a < 0.125f) {
+    const float x2 = a * a;
+    return x2 * fmaf(x2, fmaf(x2, 1.f / 45.f, -1.f / 12.f), 0.5f);
+  }
   return a + log1pf(expf(-2.f * a)) - 0.69314718055994531f;
 }
 
@@ -172,13 +184,14 @@ __device__ __forceinline__ float sample_pen(const BoxRows& b, float ux, float uy
   return phi;
 }
 
-template <int DMAX>
 __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ProblemView s_prob;
   __shared__ int s_axis[kMaxDof];
+  __shared__ int s_next;
 
-  const int D = a.rb.dof, M = a.rb.n_spheres, P = a.rb.n_pairs;
+  const int D = a.rb.dof, M = a.rb.n_spheres, P = a.rb.n_pairs, G = a.rb.n_groups;
+  const int GW = (G + 31) / 32;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
   const cr_params& prm = a.prm;
@@ -187,33 +200,40 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
   const bool swept = !ik && (flags & CR_SWEPT);
   const bool speed = !ik && (flags & CR_SPEED);
   const bool selfc = (flags & CR_SELF) != 0;
+  const bool store_x = a.store_x != 0;
   const float eta = prm.eta, inv_eta = 1.f / prm.eta;
   const float e2 = prm.eta_bound, inv_e2 = 1.f / prm.eta_bound;
   const float dt = prm.dt, inv2dt = 0.5f / dt;
 
-  const int G = a.rb.n_groups;
   EvalSmem L;
-  L.build(D, M, P, G, a.max_traj, a.max_states, a.max_horizon, nw);
+  L.build(D, M, P, G, a.max_traj, a.max_states, nw, store_x);
   float* s_fix = reinterpret_cast<float*>(smem + L.off_fix);
   float* s_lim = reinterpret_cast<float*>(smem + L.off_lim);
   float4* s_sph = reinterpret_cast<float4*>(smem + L.off_sph);
   int* s_link = reinterpret_cast<int*>(smem + L.off_link);
   float* s_soff = reinterpret_cast<float*>(smem + L.off_soff);
   float4* s_lbs = reinterpret_cast<float4*>(smem + L.off_lbs);
+  float* s_ldm = reinterpret_cast<float*>(smem + L.off_ldm);
   uint32_t* s_pairs = reinterpret_cast<uint32_t*>(smem + L.off_pairs);
   int4* s_grp = reinterpret_cast<int4*>(smem + L.off_grp);
   float* s_th = reinterpret_cast<float*>(smem + L.off_th);
   float* s_lt = reinterpret_cast<float*>(smem + L.off_lt);
+  float2* s_sc = reinterpret_cast<float2*>(smem + L.off_sc);
+  float4* s_x = reinterpret_cast<float4*>(smem + L.off_x);
   float4* s_sg = reinterpret_cast<float4*>(smem + L.off_sg);
+  uint32_t* s_nz = reinterpret_cast<uint32_t*>(smem + L.off_nz);
+  float* s_lm = reinterpret_cast<float*>(smem + L.off_lm);
+  const int MW = (M + 31) / 32;
   float4* s_rho = reinterpret_cast<float4*>(smem + L.off_rho);
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem + L.off_mask);  // 2 words per (state, link)
+  uint32_t* s_gmask = reinterpret_cast<uint32_t*>(smem + L.off_gmask);
   float* s_stw = reinterpret_cast<float*>(smem + L.off_stw);
   float* s_sts = reinterpret_cast<float*>(smem + L.off_sts);
   int* s_sta = reinterpret_cast<int*>(smem + L.off_sta);
   float* s_gth = reinterpret_cast<float*>(smem + L.off_gth);
   float4* s_wsph = reinterpret_cast<float4*>(smem + L.off_wsph);
-  float4* s_wlc = reinterpret_cast<float4*>(smem + L.off_wlc);
-  int* s_surv = reinterpret_cast<int*>(smem + L.off_surv);
   BoxRows* s_box = reinterpret_cast<BoxRows*>(smem + L.off_box);
+  float4* s_ee = reinterpret_cast<float4*>(smem + L.off_ee);
   float* s_sten = reinterpret_cast<float*>(smem + L.off_sten);
   float* s_pb = reinterpret_cast<float*>(smem + L.off_pb);
   float* s_db = reinterpret_cast<float*>(smem + L.off_db);
@@ -229,7 +249,10 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
     s_link[k] = a.rb.sphere_link[k];
     s_soff[k] = a.rb.sphere_off[k];
   }
-  for (int k = tid; k < D; k += nthr) s_lbs[k] = a.rb.link_bs[k];
+  for (int k = tid; k < D; k += nthr) {
+    s_lbs[k] = a.rb.link_bs[k];
+    s_ldm[k] = a.rb.link_dmax[k];
+  }
   for (int k = tid; k < P; k += nthr) s_pairs[k] = a.rb.pairs[k];
   for (int k = tid; k < G; k += nthr) s_grp[k] = a.rb.groups[k];
   for (int k = tid; k < D; k += nthr) s_axis[k] = a.rb.axis[k];
@@ -239,7 +262,6 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
 
   // Tiles are taken in order from a device counter (persistent launch over
   // uneven problems) or strided by the grid.
-  __shared__ int s_next;
   int tile = blockIdx.x;
   if (a.queue) {
     if (tid == 0) s_next = atomicAdd(a.queue, 1);
@@ -277,12 +299,22 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
       s_goal[k] = 0.f;
     }
     for (int k = tid; k < S * M; k += nthr) s_sg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = tid; k < S * GW; k += nthr) s_gmask[k] = 0u;
+    for (int k = tid; k < S * MW; k += nthr) s_nz[k] = 0u;
+    __syncthreads();
+    // joint sines and cosines of every slot, all threads at once
+    for (int k = tid; k < (1 + S) * D; k += nthr) {
+      const int s = k / D, j = k % D;
+      float sn, cs;
+      sincosf(s == 0 ? s_prob.q_start[j] : s_th[(s - 1) * D + j], &sn, &cs);
+      s_sc[k] = make_float2(sn, cs);
+    }
     __syncthreads();
 
     // ---- forward kinematics: slot 0 = start state, slot 1 + sigma = state sigma
     for (int s = tid; s < 1 + S; s += nthr) {
       const float* q = s == 0 ? s_prob.q_start : s_th + (s - 1) * D;
-      fk_chain(s_fix, s_axis, D, q, s_lt + s * D * 12);
+      fk_chain(s_fix, s_axis, D, q, s_sc + s * D, s_lt + s * D * 12);
     }
     __syncthreads();
 
@@ -296,26 +328,117 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
       float4 c = s_sph[i];
       return tf_point(s_lt + (sl * D + s_link[i]) * 12, c.x, c.y, c.z);
     };
+    // world position of sphere i at slot sl (stored, or from the transforms)
+    auto pos = [&](int sl, int i) -> V3 {
+      if (store_x) {
+        const float4 v = s_x[sl * M + i];
+        return v3(v.x, v.y, v.z);
+      }
+      return sphere_at(sl, i);
+    };
+    if (store_x) {
+      for (int k = tid; k < (1 + S) * M; k += nthr) {
+        const int sl = k / M, i = k % M;
+        const V3 x = sphere_at(sl, i);
+        s_x[k] = make_float4(x.x, x.y, x.z, s_sph[i].w);
+      }
+    }
+    // Link bounding-sphere centre at each state and its reach: a box farther
+    // than the reach from the centre can add nothing for any sphere of the
+    // link.  Every point of the link at offset d from its centre moves by at
+    // most |dc| + |dR|_F d to a neighbouring state, so half of that bounds the
+    // sweep length L of each of its spheres, and reach = R_link + max(eta, L).
+    for (int k = tid; k < S * D; k += nthr) {
+      const int sg = k / D, l = k % D;
+      const int r = sg / H, t = sg % H + 1;
+      const float4 lb = s_lbs[l];
+      const float* T1 = s_lt + (slot(r, t) * D + l) * 12;
+      const V3 c = tf_point(T1, lb.x, lb.y, lb.z);
+      float reach = __int_as_float(0xff800000);  // -inf: no enabled sphere
+      float Lm = 0.f;
+      if (lb.w >= 0.f) {
+        if (swept) {
+#pragma unroll
+          for (int side = -1; side <= 1; side += 2) {
+            const float* T2 = s_lt + (slot(r, t + side) * D + l) * 12;
+            const V3 c2 = tf_point(T2, lb.x, lb.y, lb.z);
+            float f = 0.f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+              for (int w = 0; w < 3; ++w) {
+                const float d = T2[4 * q + w] - T1[4 * q + w];
+                f = fmaf(d, d, f);
+              }
+            Lm = fmaxf(Lm, 0.5f * (norm(c2 - c) + sqrtf(f) * s_ldm[l]));
+          }
+        }
+        reach = lb.w + fmaxf(eta, Lm);
+      }
+      s_rho[k] = make_float4(c.x, c.y, c.z, reach);
+      s_lm[k] = fmaxf(eta, Lm);  // bounds (thr - radius) of every sphere of the link
+    }
+    // Eq. 14 pose cost at the last state of each trajectory, on the last
+    // threads of the CTA (idle in the link pass above for short tiles)
+    for (int r = nthr - 1 - tid; r >= 0 && r < nt; r += nthr) {
+      const float* LTt = s_lt + slot(r, H) * D * 12;
+      const float* T6 = LTt + (D - 1) * 12;
+      const float* Fe = s_fix + D * 12;
+      float E[12];
+#pragma unroll
+      for (int rr = 0; rr < 3; ++rr) {
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          float v = fmaf(T6[4 * rr], Fe[cc], fmaf(T6[4 * rr + 1], Fe[4 + cc], T6[4 * rr + 2] * Fe[8 + cc]));
+          E[4 * rr + cc] = cc == 3 ? v + T6[4 * rr + 3] : v;
+        }
+      }
+      const V3 e = v3(E[3] - s_prob.goal_p[0], E[7] - s_prob.goal_p[1], E[11] - s_prob.goal_p[2]);
+      const float rn = norm(e);
+      float tr = 0.f;
+#pragma unroll
+      for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) tr = fmaf(s_prob.goal_R[aa * 3 + bb], E[aa * 4 + bb], tr);
+      const float dq = (3.f - tr) * 0.25f;
+      s_goal[r] = prm.w_goal_pos * logcoshf(prm.k_goal_pos * rn) +
+                  prm.w_goal_rot * logcoshf(prm.k_goal_rot * dq);
+      const float fp = rn > 1e-30f ? prm.w_goal_pos * prm.k_goal_pos * tanhf(prm.k_goal_pos * rn) / rn
+                                   : prm.w_goal_pos * prm.k_goal_pos * prm.k_goal_pos;
+      const V3 dp = fp * e;
+      const float fr = -0.25f * prm.w_goal_rot * prm.k_goal_rot * tanhf(prm.k_goal_rot * dq);
+      // d cost / d R = fr R_g; its effect on joint j is a_j . sum_c R_c x dR_c
+      V3 w = v3(0.f, 0.f, 0.f);
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        const V3 Rc = v3(E[cc], E[4 + cc], E[8 + cc]);
+        const V3 Gc = fr * v3(s_prob.goal_R[cc], s_prob.goal_R[3 + cc], s_prob.goal_R[6 + cc]);
+        w = w + cross(Rc, Gc);
+      }
+      s_ee[3 * r] = make_float4(dp.x, dp.y, dp.z, 0.f);
+      s_ee[3 * r + 1] = make_float4(w.x, w.y, w.z, 0.f);
+      s_ee[3 * r + 2] = make_float4(E[3], E[7], E[11], 0.f);
+    }
+    __syncthreads();
 
-    // Neighbour positions of sphere i at state (r, t) for the sweep: the
-    // half distances L0, L2 to the previous / next waypoint and the unit
-    // directions.  thr = r + max(eta, L0, L2): a box farther than thr from
-    // the centre can add nothing (waypoint outside eta, no sweep sample
-    // reaches it) and is clear.
+    // Neighbour positions of sphere i at state (r, t) for the sweep: half
+    // distances L0, L2 to the previous / next waypoint and unit directions.
+    // thr = r + max(eta, L0, L2): a box farther than thr from the centre can
+    // add nothing (waypoint outside eta, no sweep sample reaches it).
     struct SphereMotion {
       V3 x1, dir0, dir2;
       float L0, L2, thr;
     };
     auto motion = [&](int r, int t, int i) -> SphereMotion {
       SphereMotion mo;
-      mo.x1 = sphere_at(slot(r, t), i);
+      mo.x1 = pos(slot(r, t), i);
       mo.dir0 = v3(0.f, 0.f, 0.f);
       mo.dir2 = mo.dir0;
       mo.L0 = 0.f;
       mo.L2 = 0.f;
       if (swept) {
-        const V3 d0 = sphere_at(slot(r, t - 1), i) - mo.x1;
-        const V3 d2 = sphere_at(slot(r, t + 1), i) - mo.x1;
+        const V3 d0 = pos(slot(r, t - 1), i) - mo.x1;
+        const V3 d2 = pos(slot(r, t + 1), i) - mo.x1;
         const float n0 = norm(d0), n2 = norm(d2);
         mo.L0 = 0.5f * n0;
         mo.L2 = 0.5f * n2;
@@ -327,165 +450,155 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
     };
 
     // ---- world term (Eq. 11 with the sweep of Sec. 3.4)
-    // (1) per state and link: link bounding-sphere centre and reach
-    //     rho_l = max over its spheres of (offset + thr): a box whose distance
-    //     to the centre is at least rho_l cannot touch any sphere of the link.
-    for (int sg = warp; sg < S; sg += nw) {
-      const int r = sg / H, t = sg % H + 1;
-      float4* rho = s_rho + sg * D;
-      if (lane < D) {
-        const float4 lb = s_lbs[lane];
-        const V3 c = tf_point(s_lt + (slot(r, t) * D + lane) * 12, lb.x, lb.y, lb.z);
-        rho[lane] = make_float4(c.x, c.y, c.z, __int_as_float(0xff800000));  // -inf
-      }
-      __syncwarp();
-      if (K > 0) {
-        for (int i = lane; i < M; i += 32) {
-          if (s_sph[i].w < 0.f) continue;
-          const SphereMotion mo = motion(r, t, i);
-          atomicMax(reinterpret_cast<int*>(&rho[s_link[i]].w), __float_as_int(s_soff[i] + mo.thr));
+    if (K > 0) {
+      for (int c0 = 0; c0 < K; c0 += kBoxChunk) {
+        const int kc = min(kBoxChunk, K - c0);
+        __syncthreads();
+        {
+          const float4* src = reinterpret_cast<const float4*>(s_prob.boxes + c0);
+          float4* dst = reinterpret_cast<float4*>(s_box);
+          for (int k = tid; k < kc * 4; k += nthr) dst[k] = src[k];
         }
-      }
-      __syncwarp();
-    }
-    // (2) box chunk by box chunk: lanes test (link, box) pairs against the
-    //     reach; surviving pairs, in (link, box) order, send the link's
-    //     spheres through the per-sphere test and, when near, the sweep.
-    for (int c0 = 0; c0 < K; c0 += kBoxChunk) {
-      const int kc = min(kBoxChunk, K - c0);
-      __syncthreads();
-      {
-        const float4* src = reinterpret_cast<const float4*>(s_prob.boxes + c0);
-        float4* dst = reinterpret_cast<float4*>(s_box);
-        for (int k = tid; k < kc * 4; k += nthr) dst[k] = src[k];
-      }
-      __syncthreads();
-      int* surv = s_surv + warp * kSurvivors;
-      for (int sg = warp; sg < S; sg += nw) {
-        const int r = sg / H, t = sg % H + 1;
-        const float4* rho = s_rho + sg * D;
-        const int n_lk = D * kc;
-        for (int p0 = 0; p0 < n_lk;) {
-          // list up to kSurvivors surviving (link, box) pairs starting at p0
-          int n_s = 0, p = p0;
-          for (; p < n_lk && n_s <= kSurvivors - 32; p += 32) {
-            const int q = p + lane;
-            bool keep = false;
-            if (q < n_lk) {
-              const int l = q / kc, kk = q % kc;
-              const float4 lc = rho[l];
-              if (lc.w >= 0.f) {
-                const BoxRows& b = s_box[kk];
-                const float ux = fmaf(b.r0.x, lc.x, fmaf(b.r0.y, lc.y, fmaf(b.r0.z, lc.z, b.r0.w)));
-                const float uy = fmaf(b.r1.x, lc.x, fmaf(b.r1.y, lc.y, fmaf(b.r1.z, lc.z, b.r1.w)));
-                const float uz = fmaf(b.r2.x, lc.x, fmaf(b.r2.y, lc.y, fmaf(b.r2.z, lc.z, b.r2.w)));
-                const float mx = fmaxf(fabsf(ux) - b.h.x, 0.f);
-                const float my = fmaxf(fabsf(uy) - b.h.y, 0.f);
-                const float mz = fmaxf(fabsf(uz) - b.h.z, 0.f);
-                keep = fmaf(mx, mx, fmaf(my, my, mz * mz)) < lc.w * lc.w;
-              }
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (keep) surv[n_s + __popc(bal & ((1u << lane) - 1u))] = q;
-            n_s += __popc(bal);
-          }
-          p0 = p;
-          __syncwarp();
-          for (int u = 0; u < n_s; ++u) {
-            const int q = surv[u];
-            const int l = q / kc, kk = q % kc;
-            const BoxRows b = s_box[kk];
-            for (int i = lane; i < M; i += 32) {
-              const float rad = s_sph[i].w;
-              if (s_link[i] != l || rad < 0.f) continue;
-              const SphereMotion mo = motion(r, t, i);
-              const V3 x1 = mo.x1;
-              const float ux = fmaf(b.r0.x, x1.x, fmaf(b.r0.y, x1.y, fmaf(b.r0.z, x1.z, b.r0.w)));
-              const float uy = fmaf(b.r1.x, x1.x, fmaf(b.r1.y, x1.y, fmaf(b.r1.z, x1.z, b.r1.w)));
-              const float uz = fmaf(b.r2.x, x1.x, fmaf(b.r2.y, x1.y, fmaf(b.r2.z, x1.z, b.r2.w)));
+        __syncthreads();
+        // (1) per (state, link): bitmask of the boxes within reach
+        for (int k = tid; k < S * D; k += nthr) {
+          const float4 lc = s_rho[k];
+          unsigned long long m = 0ull;
+          if (lc.w >= 0.f) {
+            const float rr = lc.w * lc.w;
+#pragma unroll 4
+            for (int kk = 0; kk < kc; ++kk) {
+              const BoxRows& b = s_box[kk];
+              const float ux = fmaf(b.r0.x, lc.x, fmaf(b.r0.y, lc.y, fmaf(b.r0.z, lc.z, b.r0.w)));
+              const float uy = fmaf(b.r1.x, lc.x, fmaf(b.r1.y, lc.y, fmaf(b.r1.z, lc.z, b.r1.w)));
+              const float uz = fmaf(b.r2.x, lc.x, fmaf(b.r2.y, lc.y, fmaf(b.r2.z, lc.z, b.r2.w)));
               const float mx = fmaxf(fabsf(ux) - b.h.x, 0.f);
               const float my = fmaxf(fabsf(uy) - b.h.y, 0.f);
               const float mz = fmaxf(fabsf(uz) - b.h.z, 0.f);
-              if (fmaf(mx, mx, fmaf(my, my, mz * mz)) >= mo.thr * mo.thr) continue;
-              // waypoint, then the two half-way sweeps
-              SweepAcc sw{0.f, v3(0.f, 0.f, 0.f)};
-              bool hit;
-              const float phi1 = sample_pen(b, ux, uy, uz, rad, eta, inv_eta, sw, hit);
-              if (!(phi1 - rad > 0.f)) s_free[r] = 0;
-              const float u0 = hit ? rad + eta : phi1 - rad;
-              if (swept) {
-#pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                  const float Ls = side == 0 ? mo.L0 : mo.L2;
-                  if (!(Ls > 0.f)) continue;
-                  const V3 dw = side == 0 ? mo.dir0 : mo.dir2;
-                  // direction in the box frame (rotation only)
-                  const float dx = fmaf(b.r0.x, dw.x, fmaf(b.r0.y, dw.y, b.r0.z * dw.z));
-                  const float dy = fmaf(b.r1.x, dw.x, fmaf(b.r1.y, dw.y, b.r1.z * dw.z));
-                  const float dz = fmaf(b.r2.x, dw.x, fmaf(b.r2.y, dw.y, b.r2.z * dw.z));
-                  float u = u0;
-                  for (int st = 0; st < prm.sweep_steps; ++st) {
-                    if (u >= Ls) break;
-                    const float phi = sample_pen(b, fmaf(u, dx, ux), fmaf(u, dy, uy), fmaf(u, dz, uz),
-                                                 rad, eta, inv_eta, sw, hit);
-                    u += hit ? rad + eta : phi - rad;
-                  }
-                }
-              }
-              // box frame -> world frame: grad_x = R grad_u, R = (R^T)^T
-              float4 acc4 = s_sg[sg * M + i];
-              acc4.x += sw.S;
-              acc4.y += fmaf(b.r0.x, sw.g.x, fmaf(b.r1.x, sw.g.y, b.r2.x * sw.g.z));
-              acc4.z += fmaf(b.r0.y, sw.g.x, fmaf(b.r1.y, sw.g.y, b.r2.y * sw.g.z));
-              acc4.w += fmaf(b.r0.z, sw.g.x, fmaf(b.r1.z, sw.g.y, b.r2.z * sw.g.z));
-              s_sg[sg * M + i] = acc4;
+              if (fmaf(mx, mx, fmaf(my, my, mz * mz)) < rr) m |= 1ull << kk;
             }
           }
-          __syncwarp();
+          s_mask[2 * k] = (uint32_t)m;
+          s_mask[2 * k + 1] = (uint32_t)(m >> 32);
+        }
+        __syncthreads();
+        // (2) per (state, sphere): the boxes of its link's mask in box order
+        for (int k = tid; k < S * M; k += nthr) {
+          const int sg = k / M, i = k % M;
+          const float rad = s_sph[i].w;
+          if (rad < 0.f) continue;
+          const int sl0 = sg * D + s_link[i];
+          unsigned long long m0 = (unsigned long long)s_mask[2 * sl0] | ((unsigned long long)s_mask[2 * sl0 + 1] << 32);
+          if (!m0) continue;
+          const int r = sg / H;
+          // boxes within the link-level bound of this sphere's reach first
+          unsigned long long m = 0ull;
+          {
+            const V3 xp = pos(slot(r, sg % H + 1), i);
+            const float tu = rad + s_lm[sg * D + s_link[i]];
+            while (m0) {
+              const int kk = __ffsll((long long)m0) - 1;
+              m0 &= m0 - 1ull;
+              const BoxRows& b = s_box[kk];
+              const float ux = fmaf(b.r0.x, xp.x, fmaf(b.r0.y, xp.y, fmaf(b.r0.z, xp.z, b.r0.w)));
+              const float uy = fmaf(b.r1.x, xp.x, fmaf(b.r1.y, xp.y, fmaf(b.r1.z, xp.z, b.r1.w)));
+              const float uz = fmaf(b.r2.x, xp.x, fmaf(b.r2.y, xp.y, fmaf(b.r2.z, xp.z, b.r2.w)));
+              const float mx = fmaxf(fabsf(ux) - b.h.x, 0.f);
+              const float my = fmaxf(fabsf(uy) - b.h.y, 0.f);
+              const float mz = fmaxf(fabsf(uz) - b.h.z, 0.f);
+              if (fmaf(mx, mx, fmaf(my, my, mz * mz)) < tu * tu) m |= 1ull << kk;
+            }
+          }
+          if (!m) continue;
+          const SphereMotion mo = motion(r, sg % H + 1, i);
+          const V3 x1 = mo.x1;
+          float4 acc4 = s_sg[k];
+          bool clear = true;
+          while (m) {
+            const int kk = __ffsll((long long)m) - 1;
+            m &= m - 1ull;
+            const BoxRows b = s_box[kk];
+            const float ux = fmaf(b.r0.x, x1.x, fmaf(b.r0.y, x1.y, fmaf(b.r0.z, x1.z, b.r0.w)));
+            const float uy = fmaf(b.r1.x, x1.x, fmaf(b.r1.y, x1.y, fmaf(b.r1.z, x1.z, b.r1.w)));
+            const float uz = fmaf(b.r2.x, x1.x, fmaf(b.r2.y, x1.y, fmaf(b.r2.z, x1.z, b.r2.w)));
+            const float mx = fmaxf(fabsf(ux) - b.h.x, 0.f);
+            const float my = fmaxf(fabsf(uy) - b.h.y, 0.f);
+            const float mz = fmaxf(fabsf(uz) - b.h.z, 0.f);
+            if (fmaf(mx, mx, fmaf(my, my, mz * mz)) >= mo.thr * mo.thr) continue;
+            // waypoint, then the two half-way sweeps
+            SweepAcc sw{0.f, v3(0.f, 0.f, 0.f)};
+            bool hit;
+            const float phi1 = sample_pen(b, ux, uy, uz, rad, eta, inv_eta, sw, hit);
+            if (!(phi1 - rad > 0.f)) clear = false;
+            const float u0 = hit ? rad + eta : phi1 - rad;
+            if (swept) {
+#pragma unroll
+              for (int side = 0; side < 2; ++side) {
+                const float Ls = side == 0 ? mo.L0 : mo.L2;
+                if (!(Ls > 0.f)) continue;
+                const V3 dw = side == 0 ? mo.dir0 : mo.dir2;
+                // direction in the box frame (rotation only)
+                const float dx = fmaf(b.r0.x, dw.x, fmaf(b.r0.y, dw.y, b.r0.z * dw.z));
+                const float dy = fmaf(b.r1.x, dw.x, fmaf(b.r1.y, dw.y, b.r1.z * dw.z));
+                const float dz = fmaf(b.r2.x, dw.x, fmaf(b.r2.y, dw.y, b.r2.z * dw.z));
+                float u = u0;
+                for (int st = 0; st < prm.sweep_steps; ++st) {
+                  if (u >= Ls) break;
+                  const float phi = sample_pen(b, fmaf(u, dx, ux), fmaf(u, dy, uy), fmaf(u, dz, uz),
+                                               rad, eta, inv_eta, sw, hit);
+                  u += hit ? rad + eta : phi - rad;
+                }
+              }
+            }
+            // box frame -> world frame: grad_x = R grad_u, R = (R^T)^T
+            acc4.x += sw.S;
+            acc4.y += fmaf(b.r0.x, sw.g.x, fmaf(b.r1.x, sw.g.y, b.r2.x * sw.g.z));
+            acc4.z += fmaf(b.r0.y, sw.g.x, fmaf(b.r1.y, sw.g.y, b.r2.y * sw.g.z));
+            acc4.w += fmaf(b.r0.z, sw.g.x, fmaf(b.r1.z, sw.g.y, b.r2.z * sw.g.z));
+          }
+          s_sg[k] = acc4;
+          if (!clear) s_free[r] = 0;
         }
       }
     }
 
-    // ---- self-collision (Eq. 9): largest penetration over the pair set per
-    // state; link pairs whose bounding spheres are 1 mm apart are skipped
+    // ---- self-collision (Eq. 9): link pairs whose bounding spheres are more
+    // than 1 mm apart are skipped; the rest are searched pair by pair
+    for (int k = tid; k < S * G; k += nthr) {
+      const int sg = k / G, g = k % G;
+      const int4 gr = s_grp[g];
+      const float4 A = s_rho[sg * D + gr.x], B = s_rho[sg * D + gr.y];
+      const float ra = s_lbs[gr.x].w, rb = s_lbs[gr.y].w;
+      if (ra >= 0.f && rb >= 0.f) {
+        const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
+        const float lim = ra + rb + 1e-3f;
+        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < lim * lim) atomicOr(&s_gmask[sg * GW + g / 32], 1u << (g % 32));
+      }
+    }
+    __syncthreads();
     for (int sg = warp; sg < S; sg += nw) {
       const int r = sg / H, t = sg % H + 1;
-      float4* wsp = s_wsph + warp * M;
-      float4* wlc = s_wlc + warp * D;
-      for (int i = lane; i < M; i += 32) {
-        V3 x = sphere_at(slot(r, t), i);
-        wsp[i] = make_float4(x.x, x.y, x.z, s_sph[i].w);
+      const int sl = slot(r, t);
+      const float4* X = store_x ? s_x + sl * M : s_wsph + warp * M;
+      if (!store_x) {
+        for (int i = lane; i < M; i += 32) {
+          const V3 x = sphere_at(sl, i);
+          s_wsph[warp * M + i] = make_float4(x.x, x.y, x.z, s_sph[i].w);
+        }
+        __syncwarp();
       }
-      if (lane < D) {
-        const float4 lb = s_lbs[lane];
-        const V3 c = tf_point(s_lt + (slot(r, t) * D + lane) * 12, lb.x, lb.y, lb.z);
-        wlc[lane] = make_float4(c.x, c.y, c.z, lb.w);
-      }
-      __syncwarp();
       float best = 0.f;
       int arg = -1, arg_orig = 0x7fffffff;
       bool touch = false;
-      for (int g0 = 0; g0 < G; g0 += 32) {
-        bool near = false;
-        int4 gr = make_int4(0, 0, 0, 0);
-        if (g0 + lane < G) {
-          gr = s_grp[g0 + lane];
-          const float4 A = wlc[gr.x], B = wlc[gr.y];
-          if (A.w >= 0.f && B.w >= 0.f) {
-            const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
-            const float lim = A.w + B.w + 1e-3f;
-            near = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < lim * lim;
-          }
-        }
-        unsigned bal = __ballot_sync(0xffffffffu, near);
-        while (bal) {
-          const int src = __ffs(bal) - 1;
-          bal &= bal - 1u;
-          const int first = __shfl_sync(0xffffffffu, gr.z, src);
-          const int count = __shfl_sync(0xffffffffu, gr.w, src);
-          for (int p = first + lane; p < first + count; p += 32) {
+      for (int w = 0; w < GW; ++w) {
+        uint32_t gm = s_gmask[sg * GW + w];
+        while (gm) {
+          const int g = w * 32 + __ffs(gm) - 1;
+          gm &= gm - 1u;
+          const int4 gr = s_grp[g];
+          for (int p = gr.z + lane; p < gr.z + gr.w; p += 32) {
             const uint32_t pr = s_pairs[p];
-            const float4 A = wsp[pr & 0xffffu], B = wsp[pr >> 16];
+            const float4 A = X[pr & 0xffffu], B = X[pr >> 16];
             if (A.w <= 0.f || B.w <= 0.f) continue;
             const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
             const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -529,134 +642,124 @@ __global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a
     }
     __syncthreads();
 
-    // ---- backward: d cost / d sphere centre, then Jacobian-transpose to joints
-    // (App. E.1 Table "Gradient for different joint types": revolute joint j
-    // moves a point x by a_j x (x - o_j), rotates a frame R by [a_j]_x R).
-    for (int sg = warp; sg < S; sg += nw) {
+    // ---- backward (App. E.1 Table "Gradient for different joint types":
+    // revolute joint j moves a point x by a_j x (x - o_j) and rotates a frame
+    // R by [a_j]_x R).
+    // (1) per (state, sphere): d cost / d centre from the world term (own
+    //     sweep gradient scaled by the speed, plus the speed's dependence on
+    //     the neighbouring waypoints) and the self term; it replaces the sweep
+    //     gradient in place (the sum S stays for the neighbours)
+    for (int k = tid; k < S * M; k += nthr) {
+      const int sg = k / M, i = k % M;
       const int r = sg / H, t = sg % H + 1;
-      const float* LTt = s_lt + slot(r, t) * D * 12;
-      float acc[DMAX];
-#pragma unroll
-      for (int j = 0; j < DMAX; ++j) acc[j] = 0.f;
-      float wcost = 0.f;
-      const int parg = selfc ? s_sta[sg] : -1;
-      const uint32_t pr = parg >= 0 ? s_pairs[parg] : 0u;
-      const int pi = (int)(pr & 0xffffu), pj = (int)(pr >> 16);
-      for (int i = lane; i < M; i += 32) {
-        const float4 c = s_sph[i];
-        if (c.w < 0.f) continue;
-        const int l = s_link[i];
-        const V3 x = tf_point(LTt + l * 12, c.x, c.y, c.z);
-        V3 gx = v3(0.f, 0.f, 0.f);
+      const float4 c = s_sph[i];
+      float wc = 0.f;
+      V3 gx = v3(0.f, 0.f, 0.f);
+      const int parg0 = selfc ? s_sta[sg] : -1;
+      bool in_pair = false;
+      if (parg0 >= 0) {
+        const uint32_t pr = s_pairs[parg0];
+        in_pair = i == (int)(pr & 0xffffu) || i == (int)(pr >> 16);
+      }
+      {
+        // nothing reaches this sphere: its gradient and cost stay zero
+        const float4 own = s_sg[k];
+        const float Sm0 = (speed && t >= 2) ? s_sg[k - M].x : 0.f;
+        const float Sp0 = (speed && t + 1 <= H) ? s_sg[k + M].x : 0.f;
+        if (!in_pair && own.x == 0.f && own.y == 0.f && own.z == 0.f && own.w == 0.f && Sm0 == 0.f &&
+            Sp0 == 0.f)
+          continue;
+      }
+      if (c.w >= 0.f) {
+        const V3 x = pos(slot(r, t), i);
         if (K > 0) {
-          const float4 sgv = s_sg[sg * M + i];
+          const float4 sgv = s_sg[k];
           float v = 1.f;
           if (speed) {
-            const V3 d = sphere_at(slot(r, t + 1), i) - sphere_at(slot(r, t - 1), i);
+            const V3 d = pos(slot(r, t + 1), i) - pos(slot(r, t - 1), i);
             const float n = norm(d);
             v = n * inv2dt;
             // x_{H+1} := x_H, so the last state's own speed depends on it
             if (t == H && n > 0.f && sgv.x != 0.f) gx = gx + (prm.w_coll * sgv.x * inv2dt / n) * d;
             if (t >= 2) {
-              const float Sm = s_sg[(sg - 1) * M + i].x;
+              const float Sm = s_sg[k - M].x;
               if (Sm != 0.f) {
-                const V3 dm = x - sphere_at(slot(r, t - 2), i);
+                const V3 dm = x - pos(slot(r, t - 2), i);
                 const float nm = norm(dm);
                 if (nm > 0.f) gx = gx + (prm.w_coll * Sm * inv2dt / nm) * dm;
               }
             }
             if (t + 1 <= H) {
-              const float Sp = s_sg[(sg + 1) * M + i].x;
+              const float Sp = s_sg[k + M].x;
               if (Sp != 0.f) {
-                const V3 dp = sphere_at(slot(r, t + 2), i) - x;
+                const V3 dp = pos(slot(r, t + 2), i) - x;
                 const float np = norm(dp);
                 if (np > 0.f) gx = gx - (prm.w_coll * Sp * inv2dt / np) * dp;
               }
             }
           }
           gx = gx + (prm.w_coll * v) * v3(sgv.y, sgv.z, sgv.w);
-          wcost = fmaf(prm.w_coll * v, sgv.x, wcost);
+          wc = prm.w_coll * v * sgv.x;
         }
-        if (parg >= 0 && (i == pi || i == pj)) {
-          const V3 xa = i == pi ? x : sphere_at(slot(r, t), pi);
-          const V3 xb = i == pj ? x : sphere_at(slot(r, t), pj);
-          const V3 d = xa - xb;
-          const float n = norm(d);
-          if (n > 0.f) {
-            const float f = prm.w_self / n;
-            gx = gx + (i == pi ? -f : f) * d;
-          }
-        }
-        if (gx.x != 0.f || gx.y != 0.f || gx.z != 0.f) {
-#pragma unroll
-          for (int j = 0; j < DMAX; ++j) {
-            if (j <= l) {
-              const float* T = LTt + j * 12;
-              const int ax = s_axis[j];
-              const V3 aj = v3(T[ax], T[4 + ax], T[8 + ax]);
-              const V3 rel = x - v3(T[3], T[7], T[11]);
-              acc[j] = fmaf(1.f, dot(gx, cross(aj, rel)), acc[j]);
+        const int parg = selfc ? s_sta[sg] : -1;
+        if (parg >= 0) {
+          const uint32_t pr = s_pairs[parg];
+          const int pi = (int)(pr & 0xffffu), pj = (int)(pr >> 16);
+          if (i == pi || i == pj) {
+            const V3 d = pos(slot(r, t), pi) - pos(slot(r, t), pj);
+            const float n = norm(d);
+            if (n > 0.f) {
+              const float f = prm.w_self / n;
+              gx = gx + (i == pi ? -f : f) * d;
             }
           }
         }
       }
-      // Eq. 14 pose cost at the last state
-      if (t == H && lane == 0) {
-        const float* T6 = LTt + (D - 1) * 12;
-        const float* Fe = s_fix + D * 12;
-        float E[12];
-#pragma unroll
-        for (int rr = 0; rr < 3; ++rr) {
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
-            float v = fmaf(T6[4 * rr], Fe[cc], fmaf(T6[4 * rr + 1], Fe[4 + cc], T6[4 * rr + 2] * Fe[8 + cc]));
-            E[4 * rr + cc] = cc == 3 ? v + T6[4 * rr + 3] : v;
+      float* g3 = reinterpret_cast<float*>(&s_sg[k]);
+      g3[1] = gx.x;
+      g3[2] = gx.y;
+      g3[3] = gx.z;
+      if (wc != 0.f || gx.x != 0.f || gx.y != 0.f || gx.z != 0.f)
+        atomicOr(&s_nz[sg * MW + i / 32], 1u << (i % 32));
+    }
+    __syncthreads();
+    // (2) per (state, joint): sum over the spheres on links at or after the
+    //     joint of gx . (a_j x (x - o_j)), in sphere order; the joint-0 thread
+    //     also adds up the state's world cost
+    for (int k = tid; k < S * D; k += nthr) {
+      const int sg = k / D, j = k % D;
+      const int r = sg / H, t = sg % H + 1;
+      const int sl = slot(r, t);
+      const float* T = s_lt + (sl * D + j) * 12;
+      const int ax = s_axis[j];
+      const V3 aj = v3(T[ax], T[4 + ax], T[8 + ax]);
+      const V3 oj = v3(T[3], T[7], T[11]);
+      float acc = 0.f, wsum = 0.f;
+      for (int w = 0; w < MW; ++w) {
+        uint32_t bits = s_nz[sg * MW + w];
+        while (bits) {
+          const int i = w * 32 + __ffs(bits) - 1;
+          bits &= bits - 1u;
+          if (j == 0 && K > 0) {
+            // world cost of the sphere: beta_2 speed S (recomputed, few spheres)
+            const float Si = s_sg[sg * M + i].x;
+            if (Si != 0.f) {
+              float v = 1.f;
+              if (speed) v = norm(pos(slot(r, t + 1), i) - pos(slot(r, t - 1), i)) * inv2dt;
+              wsum += prm.w_coll * v * Si;
+            }
           }
-        }
-        const V3 e = v3(E[3] - s_prob.goal_p[0], E[7] - s_prob.goal_p[1], E[11] - s_prob.goal_p[2]);
-        const float rn = norm(e);
-        float tr = 0.f;
-#pragma unroll
-        for (int aa = 0; aa < 3; ++aa)
-#pragma unroll
-          for (int bb = 0; bb < 3; ++bb) tr = fmaf(s_prob.goal_R[aa * 3 + bb], E[aa * 4 + bb], tr);
-        const float dq = (3.f - tr) * 0.25f;
-        s_goal[r] = prm.w_goal_pos * logcoshf(prm.k_goal_pos * rn) +
-                    prm.w_goal_rot * logcoshf(prm.k_goal_rot * dq);
-        const float fp = rn > 1e-30f
-                             ? prm.w_goal_pos * prm.k_goal_pos * tanhf(prm.k_goal_pos * rn) / rn
-                             : prm.w_goal_pos * prm.k_goal_pos * prm.k_goal_pos;
-        const V3 dp = fp * e;
-        const float fr = -0.25f * prm.w_goal_rot * prm.k_goal_rot * tanhf(prm.k_goal_rot * dq);
-        // sum over columns c of R_c x dR_c, dR = fr R_g
-        V3 w = v3(0.f, 0.f, 0.f);
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-          const V3 Rc = v3(E[cc], E[4 + cc], E[8 + cc]);
-          const V3 Gc = fr * v3(s_prob.goal_R[cc], s_prob.goal_R[3 + cc], s_prob.goal_R[6 + cc]);
-          w = w + cross(Rc, Gc);
-        }
-        const V3 pe = v3(E[3], E[7], E[11]);
-#pragma unroll
-        for (int j = 0; j < DMAX; ++j) {
-          if (j < D) {
-            const float* T = LTt + j * 12;
-            const int ax = s_axis[j];
-            const V3 aj = v3(T[ax], T[4 + ax], T[8 + ax]);
-            const V3 rel = pe - v3(T[3], T[7], T[11]);
-            acc[j] += dot(dp, cross(aj, rel)) + dot(aj, w);
-          }
+          if (s_link[i] < j) continue;
+          const float4 g = s_sg[sg * M + i];
+          acc += dot(v3(g.y, g.z, g.w), cross(aj, pos(sl, i) - oj));
         }
       }
-      wcost = warp_sum(wcost);
-#pragma unroll
-      for (int j = 0; j < DMAX; ++j) acc[j] = warp_sum(acc[j]);
-      if (lane == 0) {
-        s_stw[sg] = wcost;
-#pragma unroll
-        for (int j = 0; j < DMAX; ++j)
-          if (j < D) s_gth[sg * D + j] = acc[j];
+      if (t == H) {
+        const float4 dp = s_ee[3 * r], w = s_ee[3 * r + 1], pe = s_ee[3 * r + 2];
+        acc += dot(v3(dp.x, dp.y, dp.z), cross(aj, v3(pe.x, pe.y, pe.z) - oj)) + dot(aj, v3(w.x, w.y, w.z));
       }
+      s_gth[k] = acc;
+      if (j == 0) s_stw[sg] = wsum;
     }
 
     // ---- Eq. 17 position bound; App. A.5 stencils with Eq. 16 and Eq. 17 on v, a, j
@@ -786,7 +889,7 @@ __global__ void k_fk(RobotView rb, const float* __restrict__ theta, int n, float
   float q[kMaxDof];
   for (int j = 0; j < D; ++j) q[j] = theta[(long long)b * D + j];
   float LT[kMaxDof * 12];
-  fk_chain(s_fix, s_axis, D, q, LT);
+  fk_chain(s_fix, s_axis, D, q, nullptr, LT);
   if (link_tf)
     for (int k = 0; k < D * 12; ++k) link_tf[(long long)b * D * 12 + k] = LT[k];
   if (ee) {
@@ -810,9 +913,8 @@ __global__ void k_fk(RobotView rb, const float* __restrict__ theta, int n, float
 }  // namespace
 
 // The largest dynamic shared memory any launch may ask for (the opt-in
-// limit) is set once per kernel and device, never lowered, so launches
-// captured in a graph stay valid whatever is launched later.
-template <int DMAX>
+// limit) is set once per device, never lowered, so launches captured in a
+// graph stay valid whatever is launched later.
 cudaError_t allow_eval_smem() {
   static unsigned done = 0;  // bit per device
   int dev = 0;
@@ -824,52 +926,60 @@ cudaError_t allow_eval_smem() {
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, k_eval<DMAX>);
+  e = cudaFuncGetAttributes(&fa, k_eval);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_eval<DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            optin - (int)fa.sharedSizeBytes);
   if (e == cudaSuccess) done |= bit;
   return e;
 }
 
 int eval_smem_limit() {
-  int dev = 0, optin = 0;
+  static int cached[32] = {};  // per device
+  int dev = 0;
   cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return optin - 1024;  // room for the kernel's static shared memory
+  int& c = cached[dev & 31];
+  if (c == 0) {
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    c = optin - 1024;  // room for the kernel's static shared memory
+  }
+  return c;
+}
+
+// Layout of a launch: sphere positions kept in shared memory when they fit.
+static EvalSmem eval_layout(const EvalArgs& a, int block, bool* store_x) {
+  EvalSmem L;
+  L.build(a.rb.dof, a.rb.n_spheres, a.rb.n_pairs, a.rb.n_groups, a.max_traj, a.max_states,
+          block / 32, true);
+  *store_x = !a.no_store_x && L.bytes <= eval_smem_limit();
+  if (!*store_x)
+    L.build(a.rb.dof, a.rb.n_spheres, a.rb.n_pairs, a.rb.n_groups, a.max_traj, a.max_states,
+            block / 32, false);
+  return L;
+}
+
+int eval_smem_bytes(const EvalArgs& a, int block) {
+  bool sx;
+  return eval_layout(a, block, &sx).bytes;
 }
 
 int eval_blocks_per_sm(const EvalArgs& a, int block) {
   const int smem = eval_smem_bytes(a, block);
   int n = 0;
-  if (a.rb.dof <= 8) {
-    allow_eval_smem<8>();
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval<8>, block, smem);
-  } else {
-    allow_eval_smem<16>();
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval<16>, block, smem);
-  }
+  allow_eval_smem();
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval, block, smem);
   return n;
 }
 
-int eval_smem_bytes(const EvalArgs& a, int block) {
-  EvalSmem L;
-  L.build(a.rb.dof, a.rb.n_spheres, a.rb.n_pairs, a.rb.n_groups, a.max_traj, a.max_states,
-          a.max_horizon, block / 32);
-  return L.bytes;
-}
-
-cudaError_t launch_eval(const EvalArgs& a, int grid, int block, cudaStream_t stream) {
-  const int smem = eval_smem_bytes(a, block);
-  if (a.rb.dof <= 8) {
-    cudaError_t e = allow_eval_smem<8>();
-    if (e != cudaSuccess) return e;
-    k_eval<8><<<grid, block, smem, stream>>>(a);
-  } else {
-    cudaError_t e = allow_eval_smem<16>();
-    if (e != cudaSuccess) return e;
-    k_eval<16><<<grid, block, smem, stream>>>(a);
-  }
+cudaError_t launch_eval(const EvalArgs& a_in, int grid, int block, cudaStream_t stream) {
+  EvalArgs a = a_in;
+  bool sx;
+  const int smem = eval_layout(a, block, &sx).bytes;
+  a.store_x = sx ? 1 : 0;
+  cudaError_t e = allow_eval_smem();
+  if (e != cudaSuccess) return e;
+  k_eval<<<grid, block, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -91,16 +91,22 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
   const int tid = threadIdx.x;
   const int D = a.dof, m = a.prm.history, na = a.prm.n_alpha;
   const cr_opt_state& st = a.st;
+  // the evaluation that ran before this launch is complete: its work counter
+  // can start over for the next one (saves a memset node per iteration)
+  if (a.reset_queue && blockIdx.x == 0 && tid == 0) *a.reset_queue = 0;
 
-  for (int b = blockIdx.x; b < a.n_seeds; b += gridDim.x) {
-    int n, vo;
+  for (int bt = blockIdx.x; bt < a.n_seeds; bt += gridDim.x) {
+    // b: the seed's index in the per-seed arrays (the table may list a subset)
+    int n, vo, b;
     if (a.seed_tab) {
-      const int4 e = a.seed_tab[b];
+      const int4 e = a.seed_tab[bt];
       n = e.x;
       vo = e.y;
+      b = e.z;
     } else {
       n = a.horizon * D;
-      vo = b * n;
+      vo = bt * n;
+      b = bt;
     }
     float* x = st.x + vo;
     float* g = st.g + vo;

@@ -124,7 +124,7 @@ extern "C" cr_status cr_eval_batch_noalloc(const cr_robot* robot, int32_t n_prob
   a.grad = grad;
   a.cfree = cfree;
   a.terms = terms;
-  const int block = 256;
+  const int block = kEvalBlock;
   if (eval_smem_bytes(a, block) > eval_smem_limit())
     return fail(CR_EINVAL, "cr_eval_batch_noalloc: a tile needs more than 227 KB of shared memory");
   int n_sm = 0;

@@ -47,15 +47,6 @@ cr_status failf(cr_status code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return failf(CR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-// per-problem output pointers for the finishing kernel
-struct ResultView {
-  float* traj;
-  float* cost;
-  uint8_t* cfree;
-  int* best;
-  int n_seeds, n, seed_base, var_base;
-};
-
 // Best seed per problem: the lowest-cost collision-free seed, else the
 // lowest-cost seed (App. A.9 picks among valid seeds); copy out every seed's
 // best iterate, cost and flag.
@@ -92,6 +83,17 @@ __global__ void k_finish(const ResultView* res, int n_problems, const float* bes
   }
 }
 
+}  // namespace
+
+cudaError_t crgb::launch_finish(const ResultView* res, int n_problems, const float* best_x,
+                                const float* best_c, const uint8_t* best_cfree, cudaStream_t s) {
+  if (n_problems <= 0) return cudaSuccess;
+  k_finish<<<n_problems, 256, 0, s>>>(res, n_problems, best_x, best_c, best_cfree);
+  return cudaGetLastError();
+}
+
+namespace {
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -120,6 +122,8 @@ struct Plan {
   std::vector<int4> tiles_x, tiles_c, seedtab;
   std::vector<ResultView> results;
   int max_traj_x = 0, max_states_x = 0, max_traj_c = 0, max_states_c = 0, max_h = 0;
+  int block = kEvalBlock;
+  int no_store_x = 0;
   // workspace offsets (bytes)
   size_t o_x, o_g, o_xp, o_gp, o_dir, o_bx, o_c, o_bc, o_rho, o_it, o_s, o_y, o_cand, o_cgrad,
       o_ccost, o_cfree, o_bfree, o_ls, o_queue, ws_bytes;
@@ -136,11 +140,11 @@ struct cr_ctx {
   unsigned char* tab_pinned = nullptr;
   size_t tab_pinned_bytes = 0;
   cudaEvent_t staged = nullptr;  // recorded after the last copy out of tab_pinned
-  int block = 256;
   // graph cache: key bytes -> executable graph
   std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
-  // autotune table: key (M, K bucket, H) -> (block, trajectories per tile for short horizons)
-  std::map<long long, int2> tune;
+  // autotune table: (spheres, box-count bucket, horizon) -> (CTA threads,
+  // states per tile for horizons below 32)
+  std::map<long long, int4> tune;  // (block, short_tile, no position cache, -)
   ~cr_ctx() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
     if (cap) cudaStreamDestroy(cap);
@@ -151,7 +155,24 @@ struct cr_ctx {
 
 namespace {
 
-int traj_per_tile(int H) { return H >= 32 ? 1 : (32 + H - 1) / H; }
+// Tile shape of a problem: whole trajectories per tile; horizons below 32
+// pack ceil(short_tile / H) trajectories so a tile holds about short_tile states.
+int traj_per_tile(int H, int short_tile = 32) { return H >= 32 ? 1 : (short_tile + H - 1) / H; }
+
+int pow2_bucket(int K) {
+  int b = 1;
+  while (b < K) b <<= 1;
+  return b;
+}
+
+long long tune_key(int M, int K, int H) { return ((long long)M << 40) | ((long long)pow2_bucket(K) << 16) | H; }
+
+// tuned (block, short_tile, no position cache) for a problem shape, else the defaults
+int4 tuned(const cr_ctx* ctx, int M, int K, int H) {
+  auto it = ctx->tune.find(tune_key(M, K, H));
+  if (it != ctx->tune.end()) return it->second;
+  return make_int4(kEvalBlock, 32, 0, 0);
+}
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -184,7 +205,7 @@ cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* p
     pc.traj_base = sb * pl.na;
     pc.var_base = vo * pl.na;
     pl.probs_c[p] = pc;
-    for (int b = 0; b < B; ++b) pl.seedtab.push_back(make_int4(n, (int)(vo + (long long)b * n), p, 0));
+    for (int b = 0; b < B; ++b) pl.seedtab.push_back(make_int4(n, (int)(vo + (long long)b * n), sb + b, p));
     ResultView rv;
     rv.traj = res ? res[p].traj : nullptr;
     rv.cost = res ? res[p].cost : nullptr;
@@ -200,6 +221,9 @@ cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* p
   }
   pl.S = sb;
   pl.V = vo;
+  const int4 tc = tuned(ctx, rb->n_spheres, pr[0].world->n, pr[0].horizon);
+  pl.block = tc.x;
+  pl.no_store_x = tc.z;
   if (pl.V * pl.na > (1ll << 31) - 1) return failf(CR_EINVAL, "batch too large");
   // tiles, largest first (cost ~ states x boxes), so a counter-driven
   // persistent launch ends with small tiles
@@ -207,7 +231,8 @@ cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* p
                         int& ms) {
     std::vector<std::pair<long long, int4>> tmp;
     for (int p = 0; p < P; ++p) {
-      const int H = pvs[p].horizon, nt = traj_per_tile(H);
+      const int H = pvs[p].horizon;
+      const int nt = traj_per_tile(H, tuned(ctx, rb->n_spheres, pvs[p].n_boxes, H).y);
       for (int r0 = 0; r0 < pvs[p].n_traj; r0 += nt) {
         const int c = std::min(nt, pvs[p].n_traj - r0);
         tmp.push_back({(long long)c * H * (pvs[p].n_boxes + 8), make_int4(p, r0, c, 0)});
@@ -298,18 +323,21 @@ cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* p
     a.cfree = cand ? st.cand_cfree : st.best_cfree;
     a.terms = nullptr;
     a.queue = persistent ? queue : nullptr;
+    a.no_store_x = pl.no_store_x;
     return a;
   };
   auto launch_eval_batch = [&](bool cand) -> cr_status {
     EvalArgs a = eval_args(cand);
-    const int block = ctx->block;
+    const int block = pl.block;
     const int smem = eval_smem_bytes(a, block);
     if (smem > eval_smem_limit()) return failf(CR_EINVAL, "tile needs %d bytes of shared memory", smem);
     int grid = a.n_tiles;
     if (persistent) {
       const int per_sm = std::max(1, eval_blocks_per_sm(a, block));
       grid = std::min(a.n_tiles, per_sm * ctx->n_sm);
-      RT_CUDA(cudaMemsetAsync(queue, 0, sizeof(int), s));
+      // the first evaluation starts its counter here; later ones find it
+      // zeroed by the optimiser launch that precedes them
+      if (!cand) RT_CUDA(cudaMemsetAsync(queue, 0, sizeof(int), s));
     }
     RT_CUDA(launch_eval(a, grid, block, s));
     return CR_OK;
@@ -323,6 +351,7 @@ cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* p
   o.n_seeds = pl.S;
   o.seed_tab = (const int4*)(tab + pl.o_seed);
   o.st = st;
+  o.reset_queue = persistent ? queue : nullptr;
 
   // iteration state starts empty
   RT_CUDA(cudaMemsetAsync(st.s, 0, (size_t)pl.V * pl.m * 4, s));
@@ -342,9 +371,8 @@ cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* p
     o.do_propose = it + 1 < iters;
     RT_CUDA(launch_opt(o, pl.n_max, s));
   }
-  k_finish<<<pl.P, 256, 0, s>>>((const ResultView*)(tab + pl.o_res), pl.P, st.best_x, st.best_c,
-                                st.best_cfree);
-  RT_CUDA(cudaGetLastError());
+  RT_CUDA(launch_finish((const ResultView*)(tab + pl.o_res), pl.P, st.best_x, st.best_c,
+                        st.best_cfree, s));
   return CR_OK;
 }
 
@@ -360,6 +388,8 @@ std::string graph_key(const cr_robot* rb, const cr_params* prm, const Plan& pl, 
   put(&tab, sizeof(tab));
   put(&block, sizeof(block));
   put(&pl.P, sizeof(int));
+  const int nts[3] = {(int)pl.tiles_x.size(), (int)pl.tiles_c.size(), pl.no_store_x};
+  put(nts, sizeof(nts));
   for (int p = 0; p < pl.P; ++p) {
     int shp[3] = {pl.probs_x[p].n_traj, pl.probs_x[p].horizon, pl.probs_x[p].n_boxes};
     put(shp, sizeof(shp));
@@ -453,7 +483,7 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
   if (!(solve_flags & CR_SOLVE_GRAPH)) {
     return enqueue_iterations(ctx, robot, params, pl, ws, tab, iters, persistent, st);
   }
-  const std::string key = graph_key(robot, params, pl, iters, persistent, ws, tab, ctx->block);
+  const std::string key = graph_key(robot, params, pl, iters, persistent, ws, tab, pl.block);
   cudaGraphExec_t exec = nullptr;
   for (auto& g : ctx->graphs)
     if (g.first == key) exec = g.second;
@@ -487,3 +517,71 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
 }
 
 }  // extern "C"
+
+extern "C" cr_status cr_autotune(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems,
+                                 const cr_problem* problems, const cr_params* params, int32_t iters,
+                                 int32_t* block_out, int32_t* short_tile_out, int32_t* no_cache_out,
+                                 float* ms_out) {
+  if (!ctx || !robot || !problems || n_problems < 1) return failf(CR_EINVAL, "cr_autotune: bad argument");
+  if (iters < 1) iters = 2;
+  int min_h = kMaxHorizon;
+  for (int p = 0; p < n_problems; ++p) min_h = std::min(min_h, problems[p].horizon);
+  const int blocks[2] = {256, 512};
+  std::vector<int> shorts = {32};
+  if (min_h < 32) shorts = {8, 16, 32, 64};
+  const int caches[2] = {0, 1};
+  cudaStream_t s = nullptr;
+  RT_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  RT_CUDA(cudaEventCreate(&e0));
+  RT_CUDA(cudaEventCreate(&e1));
+  // results go to scratch outputs owned by the context workspace: none needed
+  float best_ms = INFINITY;
+  int4 best = make_int4(kEvalBlock, 32, 0, 0);
+  const std::map<long long, int4> saved = ctx->tune;
+  cr_status st = CR_OK;
+  for (int bl : blocks) {
+    for (int sh : shorts)
+    for (int nc : caches) {
+      for (int p = 0; p < n_problems; ++p)
+        ctx->tune[tune_key(robot->n_spheres, problems[p].world->n, problems[p].horizon)] = make_int4(bl, sh, nc, 0);
+      // warm-up, then timed
+      st = cr_solve(ctx, robot, n_problems, problems, params, iters, CR_SOLVE_PERSISTENT, nullptr, s);
+      if (st != CR_OK) break;
+      RT_CUDA(cudaEventRecord(e0, s));
+      st = cr_solve(ctx, robot, n_problems, problems, params, iters, CR_SOLVE_PERSISTENT, nullptr, s);
+      if (st != CR_OK) break;
+      RT_CUDA(cudaEventRecord(e1, s));
+      RT_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      RT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = make_int4(bl, sh, nc, 0);
+      }
+    }
+    if (st != CR_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  ctx->tune = saved;
+  if (st != CR_OK) return st;
+  for (int p = 0; p < n_problems; ++p)
+    ctx->tune[tune_key(robot->n_spheres, problems[p].world->n, problems[p].horizon)] = best;
+  if (block_out) *block_out = best.x;
+  if (short_tile_out) *short_tile_out = best.y;
+  if (no_cache_out) *no_cache_out = best.z;
+  if (ms_out) *ms_out = best_ms;
+  return CR_OK;
+}
+
+extern "C" cr_status cr_tune_set(cr_ctx* ctx, int32_t n_spheres, int32_t n_boxes, int32_t horizon,
+                                 int32_t block, int32_t short_tile, int32_t no_cache) {
+  if (!ctx) return failf(CR_EINVAL, "cr_tune_set: null context");
+  if (block != 256 && block != 512) return failf(CR_EINVAL, "cr_tune_set: block must be 256 or 512");
+  if (short_tile < 1 || short_tile > 128) return failf(CR_EINVAL, "cr_tune_set: short_tile outside 1..128");
+  ctx->tune[tune_key(n_spheres, n_boxes, horizon)] = make_int4(block, short_tile, no_cache ? 1 : 0, 0);
+  return CR_OK;
+}
