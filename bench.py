@@ -247,8 +247,8 @@ def main():
     ap.add_argument("--impl", default="crgb")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--extras", default="ik,uneven,plain,serve")
-    ap.add_argument("--serve-rate", type=float, default=500.0)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-rates", default="500,100")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--profile", type=int, default=0,
                     help="only run N fused evaluations of one line-search batch inside the NVTX "
                          "range crgb_eval (for ncu), then exit")
@@ -408,8 +408,9 @@ def main():
         extras["uneven"] = bench_uneven(crgb, synth, ctx, R, rb)
     if rank == 0 and "serve" in want:
         from paper_2310_17274_gb300 import serve
-        extras["serve"] = serve.serving_benchmark(crgb, synth, ctx, R, rb, rate=args.serve_rate,
-                                                  seconds=args.serve_seconds, plain_seconds=2.0)
+        rates = tuple(float(r) for r in args.serve_rates.split(","))
+        extras["serve"] = serve.serving_benchmark(crgb, synth, ctx, R, rb, rates=rates,
+                                                  seconds=args.serve_seconds)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -439,8 +440,11 @@ def main():
 
 
 def bench_ik(crgb, synth, ctx, R, rb, n_goals=1000, n_seeds=32, iters=50):
-    """Batched collision-free IK: 1000 goals x 32 seeds (H = 1) in one solve;
-    solved = best seed collision-free, within 5 mm and d_q <= 1e-3."""
+    """Batched collision-free IK: 1000 goals x 32 seeds (H = 1) in one solve.
+    Solved (the paper's success test, Sec. 6: collision-free, within 5 mm and
+    5% of the goal orientation, read as the orientation distance of Eq. 14,
+    d_q = (3 - tr(R_g^T R)) / 4 in [0, 1], at most 0.05); a strict count with
+    d_q <= 1e-3 (about 3.6 degrees) is reported beside it."""
     import torch
     cfg = synth.CONFIGS["ik"]
     rng = np.random.default_rng(3)
@@ -471,6 +475,7 @@ def bench_ik(crgb, synth, ctx, R, rb, n_goals=1000, n_seeds=32, iters=50):
     goals = np.stack([np.concatenate([e[:, 3], _rot_to_quat(e[:, :3])]) for e in ee])
     seeds = synth.uniform_config(rng, rb, n_goals * n_seeds).reshape(n_goals, n_seeds, 1, rb.dof)
     specs = [crgb.ProblemSpec(W, qs, goals[g], 1, seeds=seeds[g]) for g in range(n_goals)]
+    choice = crgb.autotune(ctx, R, specs, ikp, iters=5)
     outs = None
     for _ in range(3):
         outs = crgb.solve(ctx, R, specs, ikp, iters=iters, graph=True, persistent=True, outputs=outs)
@@ -492,16 +497,21 @@ def bench_ik(crgb, synth, ctx, R, rb, n_goals=1000, n_seeds=32, iters=50):
     pos_err = np.linalg.norm(eb[:, :, 3] - goals[:, :3], axis=1)
     Rg = np.stack([_quat_rot(g[3:]) for g in goals])
     dq = (3 - np.einsum("nij,nij->n", Rg, eb[:, :, :3])) / 4
-    solved = free & (pos_err <= 5e-3) & (dq <= 1e-3)
+    solved = free & (pos_err <= 5e-3) & (dq <= 0.05)
+    strict = free & (pos_err <= 5e-3) & (dq <= 1e-3)
     if os.environ.get("CRGB_BENCH_DEBUG"):
         print("ik debug: free", free.mean(), "pos<5mm", (pos_err <= 5e-3).mean(), "dq<1e-3",
-              (dq <= 1e-3).mean(), "median pos", np.median(pos_err), "median dq", np.median(dq),
+              (dq <= 1e-3).mean(), "dq<0.05", (dq <= 0.05).mean(), "median pos", np.median(pos_err), "median dq", np.median(dq),
               "median best cost", np.median([float(o.cost[int(o.best)]) for o in outs]), file=sys.stderr)
     return {"goals": n_goals, "seeds": n_seeds, "iters": iters, "ms_per_batch": t * 1e3,
             "ik_goals_per_s": n_goals / t, "success_rate": float(solved.mean()),
             "ik_solves_per_s": float(solved.sum()) / t,
+            "success_rate_strict": float(strict.mean()),
+            "success": "collision-free, position within 5 mm, d_q <= 0.05 (strict: d_q <= 1e-3)",
+            "median_pos_err_m": float(np.median(pos_err)), "median_dq": float(np.median(dq)),
             "evals_per_s": n_goals * n_seeds * (iters * ikp.n_alpha + 1) / t,
-            "goals_from": "FK of collision-free configurations sampled within the limits"}
+            "goals_from": "FK of collision-free configurations sampled within the limits",
+            "autotune": choice}
 
 
 def _quat_rot(q):
@@ -529,6 +539,8 @@ def bench_uneven(crgb, synth, ctx, R, rb, iters=100):
         specs.append(crgb.ProblemSpec(W, qs, goal, H, seeds=seeds))
         units += iters * B * 4 * H + B * H
     P = crgb.make_params(None)
+    # tile shapes for these problem shapes from the autotuner (untimed)
+    choice = crgb.autotune(ctx, R, specs, P, iters=10)
     outs = None
     for _ in range(2):
         outs = crgb.solve(ctx, R, specs, P, iters=iters, graph=True, persistent=True, outputs=outs)
@@ -555,7 +567,8 @@ def bench_uneven(crgb, synth, ctx, R, rb, iters=100):
     return {"problems": len(specs), "iters": iters, "evals_per_step": units,
             "batched_ms": t_batched * 1e3, "batched_evals_per_s": units / t_batched,
             "plain_ms": t_plain * 1e3, "plain_evals_per_s": units / t_plain,
-            "speedup": t_plain / t_batched, "results_identical": bool(same)}
+            "speedup": t_plain / t_batched, "results_identical": bool(same),
+            "autotune": choice}
 
 
 if __name__ == "__main__":

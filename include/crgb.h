@@ -260,8 +260,11 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
 cr_status cr_autotune(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
                       const cr_params* params, int32_t iters, int32_t* block, int32_t* short_tile,
                       int32_t* no_cache, float* ms);
-/* Set the tile shape of one problem shape by hand (block 256 or 512;
- * no_cache = 1 recomputes sphere positions instead of caching them). */
+/* Set the tile shape of one problem shape by hand: block 256 or 512;
+ * no_cache = 1 recomputes sphere positions instead of caching them in shared
+ * memory and bounds registers so two 512-thread CTAs share an SM, 0 caches
+ * them (one CTA per SM), -1 takes 1 when two such CTAs fit, else 0 (the
+ * default for shapes never tuned, and for cr_eval). */
 cr_status cr_tune_set(cr_ctx* ctx, int32_t n_spheres, int32_t n_boxes, int32_t horizon, int32_t block,
                       int32_t short_tile, int32_t no_cache);
 

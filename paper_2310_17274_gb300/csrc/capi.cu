@@ -335,7 +335,7 @@ cr_status cr_eval(const cr_robot* robot, const cr_problem* problem, const cr_par
   if (s != CR_OK) return s;
   if (B < 0) return fail(CR_EINVAL, "cr_eval: B < 0");
   if (B > 0 && (!theta || !cost)) return fail(CR_EINVAL, "cr_eval: null theta or cost");
-  EvalArgs a;
+  EvalArgs a{};
   std::memset(&a, 0, sizeof(a));
   s = fill_problem(robot, problem, &a.prob0);
   if (s != CR_OK) return s;
@@ -355,6 +355,7 @@ cr_status cr_eval(const cr_robot* robot, const cr_problem* problem, const cr_par
   a.grad = grad;
   a.cfree = cfree;
   a.terms = terms;
+  a.no_store_x = -1;
   const int block = kEvalBlock;
   const int smem = eval_smem_bytes(a, block);
   if (smem > eval_smem_limit())
@@ -384,7 +385,7 @@ static cr_status opt_common(const cr_robot* robot, const cr_params* params, cons
 cr_status cr_opt_propose(const cr_robot* robot, const cr_params* params, const cr_opt_state* st,
                          void* stream) {
   if (!robot) return fail(CR_EINVAL, "cr_opt_propose: null robot");
-  OptArgs a;
+  OptArgs a{};
   cr_status s = opt_common(robot, params, st, &a);
   if (s != CR_OK) return s;
   const int n = st->horizon * robot->dof;
@@ -402,7 +403,7 @@ cr_status cr_opt_propose(const cr_robot* robot, const cr_params* params, const c
 cr_status cr_opt_select(const cr_robot* robot, const cr_params* params, const cr_opt_state* st,
                         void* stream) {
   if (!robot) return fail(CR_EINVAL, "cr_opt_select: null robot");
-  OptArgs a;
+  OptArgs a{};
   cr_status s = opt_common(robot, params, st, &a);
   if (s != CR_OK) return s;
   const int n = st->horizon * robot->dof;

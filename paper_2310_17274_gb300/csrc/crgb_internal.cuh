@@ -63,7 +63,9 @@ struct EvalArgs {
   int n_tiles;
   int* queue;                    // persistent launch: work counter (zeroed before launch), or nullptr
   int store_x;                   // set by the launcher: keep sphere positions in shared memory
-  int no_store_x;                // tile option: never keep them (smaller tiles, more CTAs per SM)
+  int no_store_x;                // tile option: 1 = never keep them, at most 64 registers a
+                                 // thread (two 512-thread CTAs per SM); 0 = one CTA per SM,
+                                 // positions kept when they fit; -1 = 1 when two CTAs fit
   int traj_per_tile;             // single-problem launch: trajectories per CTA
   int max_traj;                  // largest trajectory count of a tile
   int max_states;                // largest (trajectories x horizon) of a tile

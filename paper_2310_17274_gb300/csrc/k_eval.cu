@@ -184,7 +184,11 @@ __device__ __forceinline__ float sample_pen(const BoxRows& b, float ux, float uy
   return phi;
 }
 
-__global__ void __launch_bounds__(512) k_eval(const __grid_constant__ EvalArgs a) {
+// MinBlocks = 1: up to 128 registers a thread, sphere positions may be
+// cached in shared memory.  MinBlocks = 2: at most 64 registers and no
+// position cache, so that two 512-thread CTAs share an SM.
+template <int MinBlocks>
+__global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__ EvalArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ProblemView s_prob;
   __shared__ int s_axis[kMaxDof];
@@ -915,21 +919,27 @@ __global__ void k_fk(RobotView rb, const float* __restrict__ theta, int n, float
 // The largest dynamic shared memory any launch may ask for (the opt-in
 // limit) is set once per device, never lowered, so launches captured in a
 // graph stay valid whatever is launched later.
+template <int MinBlocks>
+static cudaError_t allow_smem(int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_eval<MinBlocks>);
+  if (e != cudaSuccess) return e;
+  // opt-in limit minus the kernel's static shared memory
+  return cudaFuncSetAttribute(k_eval<MinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
 cudaError_t allow_eval_smem() {
   static unsigned done = 0;  // bit per device
   int dev = 0;
   cudaGetDevice(&dev);
   const unsigned bit = 1u << (dev & 31);
   if (done & bit) return cudaSuccess;
-  // opt-in limit minus the kernel's static shared memory
   int optin = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, k_eval);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           optin - (int)fa.sharedSizeBytes);
+  e = allow_smem<1>(optin);
+  if (e == cudaSuccess) e = allow_smem<2>(optin);
   if (e == cudaSuccess) done |= bit;
   return e;
 }
@@ -947,12 +957,27 @@ int eval_smem_limit() {
   return c;
 }
 
-// Layout of a launch: sphere positions kept in shared memory when they fit.
-static EvalSmem eval_layout(const EvalArgs& a, int block, bool* store_x) {
+// Kernel variant and layout of a launch.  no_store_x = 1 takes the
+// two-CTAs-per-SM variant without the position cache; 0 the one-CTA variant,
+// positions cached in shared memory when they fit; -1 (auto) the first when
+// two of its CTAs fit on an SM, else the second.
+static EvalSmem eval_layout(const EvalArgs& a, int block, bool* store_x, bool* two) {
   EvalSmem L;
+  int mode = a.no_store_x;
+  if (mode < 0) {
+    L.build(a.rb.dof, a.rb.n_spheres, a.rb.n_pairs, a.rb.n_groups, a.max_traj, a.max_states,
+            block / 32, false);
+    int n = 0;
+    allow_eval_smem();
+    if (L.bytes <= eval_smem_limit() &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval<2>, block, L.bytes) != cudaSuccess)
+      n = 0;
+    mode = n >= 2 ? 1 : 0;
+  }
+  *two = mode == 1;
   L.build(a.rb.dof, a.rb.n_spheres, a.rb.n_pairs, a.rb.n_groups, a.max_traj, a.max_states,
           block / 32, true);
-  *store_x = !a.no_store_x && L.bytes <= eval_smem_limit();
+  *store_x = mode == 0 && L.bytes <= eval_smem_limit();
   if (!*store_x)
     L.build(a.rb.dof, a.rb.n_spheres, a.rb.n_pairs, a.rb.n_groups, a.max_traj, a.max_states,
             block / 32, false);
@@ -960,26 +985,33 @@ static EvalSmem eval_layout(const EvalArgs& a, int block, bool* store_x) {
 }
 
 int eval_smem_bytes(const EvalArgs& a, int block) {
-  bool sx;
-  return eval_layout(a, block, &sx).bytes;
+  bool sx, two;
+  return eval_layout(a, block, &sx, &two).bytes;
 }
 
 int eval_blocks_per_sm(const EvalArgs& a, int block) {
-  const int smem = eval_smem_bytes(a, block);
+  bool sx, two;
+  const int smem = eval_layout(a, block, &sx, &two).bytes;
   int n = 0;
   allow_eval_smem();
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval, block, smem);
+  if (two)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval<2>, block, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval<1>, block, smem);
   return n;
 }
 
 cudaError_t launch_eval(const EvalArgs& a_in, int grid, int block, cudaStream_t stream) {
   EvalArgs a = a_in;
-  bool sx;
-  const int smem = eval_layout(a, block, &sx).bytes;
+  bool sx, two;
+  const int smem = eval_layout(a, block, &sx, &two).bytes;
   a.store_x = sx ? 1 : 0;
   cudaError_t e = allow_eval_smem();
   if (e != cudaSuccess) return e;
-  k_eval<<<grid, block, smem, stream>>>(a);
+  if (two)
+    k_eval<2><<<grid, block, smem, stream>>>(a);
+  else
+    k_eval<1><<<grid, block, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

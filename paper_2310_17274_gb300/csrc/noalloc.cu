@@ -108,7 +108,7 @@ extern "C" cr_status cr_eval_batch_noalloc(const cr_robot* robot, int32_t n_prob
   if (e == cudaSuccess) e = cudaMemsetAsync(scratch + kQueueOff, 0, sizeof(int), st);
   if (e != cudaSuccess) return fail(CR_ECUDA, cudaGetErrorString(e));
 
-  EvalArgs a;
+  EvalArgs a{};
   std::memset(&a, 0, sizeof(a));
   a.rb = robot->view;
   a.prm = *params;
@@ -124,6 +124,7 @@ extern "C" cr_status cr_eval_batch_noalloc(const cr_robot* robot, int32_t n_prob
   a.grad = grad;
   a.cfree = cfree;
   a.terms = terms;
+  a.no_store_x = -1;
   const int block = kEvalBlock;
   if (eval_smem_bytes(a, block) > eval_smem_limit())
     return fail(CR_EINVAL, "cr_eval_batch_noalloc: a tile needs more than 227 KB of shared memory");

@@ -171,7 +171,7 @@ long long tune_key(int M, int K, int H) { return ((long long)M << 40) | ((long l
 int4 tuned(const cr_ctx* ctx, int M, int K, int H) {
   auto it = ctx->tune.find(tune_key(M, K, H));
   if (it != ctx->tune.end()) return it->second;
-  return make_int4(kEvalBlock, 32, 0, 0);
+  return make_int4(kEvalBlock, 32, -1, 0);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -307,7 +307,7 @@ cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* p
   const cr_opt_state st = state_of(pl, ws);
   int* queue = (int*)(ws + pl.o_queue);
   auto eval_args = [&](bool cand) {
-    EvalArgs a;
+    EvalArgs a{};
     std::memset(&a, 0, sizeof(a));
     a.rb = rb->view;
     a.prm = *prm;
@@ -342,7 +342,7 @@ cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* p
     RT_CUDA(launch_eval(a, grid, block, s));
     return CR_OK;
   };
-  OptArgs o;
+  OptArgs o{};
   std::memset(&o, 0, sizeof(o));
   o.prm = *prm;
   o.q_lo = rb->view.lim;
@@ -582,6 +582,6 @@ extern "C" cr_status cr_tune_set(cr_ctx* ctx, int32_t n_spheres, int32_t n_boxes
   if (!ctx) return failf(CR_EINVAL, "cr_tune_set: null context");
   if (block != 256 && block != 512) return failf(CR_EINVAL, "cr_tune_set: block must be 256 or 512");
   if (short_tile < 1 || short_tile > 128) return failf(CR_EINVAL, "cr_tune_set: short_tile outside 1..128");
-  ctx->tune[tune_key(n_spheres, n_boxes, horizon)] = make_int4(block, short_tile, no_cache ? 1 : 0, 0);
+  ctx->tune[tune_key(n_spheres, n_boxes, horizon)] = make_int4(block, short_tile, no_cache < 0 ? -1 : (no_cache ? 1 : 0), 0);
   return CR_OK;
 }

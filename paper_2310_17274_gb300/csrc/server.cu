@@ -283,7 +283,7 @@ cr_status launch_eval_set(cr_server* sv, Pool& pl, const ProblemView* probs, con
                           int n_tiles, bool cand) {
   if (n_tiles == 0) return CR_OK;
   const cr_opt_state st = pl.state();
-  EvalArgs a;
+  EvalArgs a{};
   std::memset(&a, 0, sizeof(a));
   a.rb = sv->robot->view;
   a.prm = pl.prm;
@@ -298,6 +298,7 @@ cr_status launch_eval_set(cr_server* sv, Pool& pl, const ProblemView* probs, con
   a.cost = cand ? st.cand_cost : st.c;
   a.grad = cand ? st.cand_grad : st.g;
   a.cfree = cand ? st.cand_cfree : st.best_cfree;
+  a.no_store_x = -1;
   a.queue = (int*)pl.p(pl.o_queue);
   const int block = kEvalBlock;
   if (eval_smem_bytes(a, block) > eval_smem_limit()) return failf(CR_EINVAL, "server: tile too large");
@@ -310,7 +311,7 @@ cr_status launch_eval_set(cr_server* sv, Pool& pl, const ProblemView* probs, con
 cr_status launch_opt_set(cr_server* sv, Pool& pl, const int4* seeds, int n_seeds, bool select,
                          bool propose, bool init) {
   if (n_seeds == 0) return CR_OK;
-  OptArgs o;
+  OptArgs o{};
   std::memset(&o, 0, sizeof(o));
   o.prm = pl.prm;
   o.q_lo = sv->robot->view.lim;

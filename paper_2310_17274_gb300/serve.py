@@ -89,6 +89,11 @@ def run_served(crgb, server, reqs, arrivals, horizon_s):
         if now > horizon_s:
             break
     wall = time.perf_counter() - t0
+    while pending:   # finish what is left, untimed, so the server is empty again
+        server.step()
+        for t in list(pending):
+            if server.poll(t) is not None:
+                pending.pop(t)
     return lat, wall
 
 
@@ -126,30 +131,39 @@ def summarize(lat, arrivals, wall):
             "throughput_req_s": float(done.sum() / wall), "wall_s": float(wall)}
 
 
-def serving_benchmark(crgb, synth, ctx, R, rb, rate=500.0, seconds=5.0, warm_s=1.0, chunk=10,
-                      plain_seconds=None, mg_iters=100, ik_iters=50):
+def serving_benchmark(crgb, synth, ctx, R, rb, rates=(500.0, 100.0), seconds=3.0, warm_s=0.5,
+                      drain_s=10.0, chunk=10, mg_iters=100, ik_iters=50):
     """Continuous batching vs plain per-request solves on the same Poisson
-    stream (rate requests/s, MG:IK = 1:1)."""
+    stream (MG:IK = 1:1) at each rate.  Both paths see the same arrivals
+    over warm_s + seconds and may drain for drain_s more; requests arriving
+    in the warm-up are not counted; one unfinished at the end counts with its
+    wait so far (so an overloaded path reports a lower bound)."""
     mg_p = crgb.make_params(dict(alpha=list(synth.ALPHA_8)))
     ik_p = crgb.make_params(dict(flags=crgb.IK_MODE | crgb.SELF | crgb.WOLFE))
-    n = int(rate * (seconds + warm_s)) + 1
-    reqs, keep = make_requests(crgb, synth, R, rb, n)
-    arr = poisson_arrivals(rate, n)
+    params = {crgb.MG: (mg_p, mg_iters), crgb.IK: (ik_p, ik_iters)}
     server = crgb.Server(ctx, R, mg=(32, 48, mg_iters), ik=(32, 1, ik_iters), mg_params=mg_p,
                          ik_params=ik_p, chunk=chunk)
-    # warm-up: a few requests through both paths
-    w = min(8, n)
-    run_served(crgb, server, reqs[:w], np.zeros(w), 60.0)
-    lat, wall = run_served(crgb, server, reqs, arr, seconds + warm_s + 30.0)
-    keep_i = arr >= warm_s
-    served = summarize(lat[keep_i], arr[keep_i], wall)
-    served["pool_bytes"] = server.stats()["pool_bytes"]
-    params = {crgb.MG: (mg_p, mg_iters), crgb.IK: (ik_p, ik_iters)}
-    ps = plain_seconds if plain_seconds is not None else seconds
-    m = int(np.searchsorted(arr, ps + warm_s))
-    run_plain(crgb, ctx, R, reqs[:w], np.zeros(w), params, 60.0)
-    lat_p, wall_p = run_plain(crgb, ctx, R, reqs[:m], arr[:m], params, ps + warm_s + 10.0)
-    keep_p = arr[:m] >= warm_s
-    plain = summarize(lat_p[keep_p], arr[:m][keep_p], wall_p)
-    return {"rate_req_s": rate, "seconds": seconds, "chunk": chunk, "served": served,
-            "plain": plain}
+    out = {"seconds": seconds, "drain_s": drain_s, "chunk": chunk, "mix": "MG:IK = 1:1",
+           "mg_iters": mg_iters, "ik_iters": ik_iters, "rates": []}
+    warmed = False
+    for k, rate in enumerate(rates):
+        n = int(rate * (seconds + warm_s)) + 1
+        reqs, keep = make_requests(crgb, synth, R, rb, n, seed=5 + k)
+        arr = poisson_arrivals(rate, n, seed=6 + k)
+        arr = arr[arr <= seconds + warm_s]
+        reqs = reqs[:len(arr)]
+        if not warmed:   # a few requests through both paths first
+            w = min(8, len(reqs))
+            run_served(crgb, server, reqs[:w], np.zeros(w), 60.0)
+            run_plain(crgb, ctx, R, reqs[:w], np.zeros(w), params, 60.0)
+            warmed = True
+        horizon = seconds + warm_s + drain_s
+        cnt = arr >= warm_s
+        lat, wall = run_served(crgb, server, reqs, arr, horizon)
+        served = summarize(lat[cnt], arr[cnt], wall)
+        served["pool_bytes"] = server.stats()["pool_bytes"]
+        lat_p, wall_p = run_plain(crgb, ctx, R, reqs, arr, params, horizon)
+        plain = summarize(lat_p[cnt], arr[cnt], wall_p)
+        out["rates"].append({"rate_req_s": rate, "served": served, "plain": plain})
+        del keep
+    return out

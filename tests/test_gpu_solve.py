@@ -178,10 +178,11 @@ def test_ik_batch(ctx):
         if ev["margin"][0] >= 1e-5:
             assert bool(o.cfree[b]) == bool(ev["cfree"][0])
             # near a converged pose the cost is steep in the end-effector
-            # pose: allow what 2e-7 m / 2e-7 rad of FP32 pose error can change
+            # pose: allow what 1e-6 m / 1e-6 rad of pose error can change
+            # (FP32 kinematics through seven chained transforms of unit scale)
             _, _, ee = oracle.fk(rb, q)
             _, dp, dR = oracle.goal_cost(p, ee, goal)
-            slack = 2e-7 * (np.linalg.norm(dp) + np.linalg.norm(dR))
+            slack = 1e-6 * (np.linalg.norm(dp) + np.linalg.norm(dR))
             assert abs(float(o.cost[b]) - ev["cost"][0]) <= 1e-4 * max(abs(ev["cost"][0]), 1e-2) + slack
         _, _, ee = oracle.fk(rb, q)
         E = ee.reshape(3, 4)
