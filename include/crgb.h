@@ -170,8 +170,10 @@ cr_status cr_eval(const cr_robot* robot, const cr_problem* problem, const cr_par
 
 /* Device-resident optimiser state of B seeds with n = H*dof variables each
  * (Sec. 4.1, App. A.7).  Every pointer is device memory owned by the caller.
- * History buffers hold the newest pair last (index m-1); zeroed buffers with
- * rho = 0 are inert.  cand* hold the n_alpha line-search candidates of each
+ * The history (s, y, rho) is a ring of m slots: the pair appended by the
+ * cr_opt_propose call that finds iter = k > 0 goes to slot (k-1) mod m, so
+ * with iter = k the i-th of the m most recent pairs (i = 0 oldest, m-1
+ * newest) is in slot (k-1+i) mod m.  Zeroed buffers with rho = 0 are inert.  cand* hold the n_alpha line-search candidates of each
  * seed, seed-major ([B][n_alpha][...]). */
 typedef struct {
   int32_t n_seeds, horizon;

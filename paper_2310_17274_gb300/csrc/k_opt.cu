@@ -1,10 +1,11 @@
 // k_opt.cu -- L-BFGS two-loop step, parallel noisy line-search selection and
 // best-iterate tracking (Sec. 4.1, Alg. 1, App. A.7), one CTA per seed.
 //
-// A seed's history (m pairs of n = H*dof floats) is pulled into shared memory
-// with one bulk load, so the 2m dependent dot products of the two-loop
-// recursion run out of shared memory; the history shift is a relabelling of
-// slots while the pairs are written back in newest-last order.
+// A seed's history (m pairs of n = H*dof floats) is a ring of m slots in
+// device memory: the pair appended when iter = k > 0 goes to slot (k-1) mod m,
+// so an iteration writes one pair and never moves the others.  The ring is
+// pulled into shared memory (all loads in flight at once) and the 2m
+// dependent dot products of the two-loop recursion run out of shared memory.
 //
 // Every dot product is reduced in one fixed order, that of a virtual block of
 // 256 threads: element k belongs to virtual thread k mod 256, which adds its
@@ -22,19 +23,21 @@ namespace crgb {
 namespace {
 
 constexpr int kVirt = 256;        // virtual threads per seed
-constexpr int kSlots = 8;         // element slots per physical thread
+constexpr int kSlots = 8;         // most element slots per physical thread
 constexpr int kMaxN = kVirt * kSlots;
 
-// Partial sums of one dot product for NT physical threads.
-template <int NT>
+// Partial sums of one dot product for NT physical threads holding SLOTS
+// element slots each (element k = tid + NT * e).  With NT = 256 every slot of
+// a thread belongs to the same virtual thread; with NT = 32 slot e is virtual
+// thread tid + 32 e.
+template <int NT, int SLOTS>
 struct Part {
-  static constexpr int kP = NT == kVirt ? 1 : kSlots;
+  static constexpr int kP = NT == kVirt ? 1 : SLOTS;
   float p[kP];
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int i = 0; i < kP; ++i) p[i] = 0.f;
   }
-  // add a*b for element slot e (element k = tid + NT * e)
   __device__ __forceinline__ void fma(int e, float a, float b) {
     if (kP == 1)
       p[0] = fmaf(a, b, p[0]);
@@ -49,10 +52,19 @@ __device__ __forceinline__ float butterfly(float s) {
   return s;
 }
 
-// Totals of V dot products; every thread gets them.
-template <int NT, int V>
-__device__ __forceinline__ void block_sum(Part<NT> (&v)[V], float (&out)[V], float* red) {
+constexpr int kRed = (kVirt / 32) * (CR_MAX_ALPHA + 1);  // one reduction buffer
+
+// Totals of V dot products; every thread gets them.  Successive calls
+// alternate between two buffers (`phase`), so one barrier per call suffices:
+// a buffer is rewritten only after the barrier of the call in between, which
+// every thread reaches after its reads of the buffer.  Virtual warps with no
+// elements add +0 in both forms, so NT = 32 and NT = 256 agree bit for bit.
+template <int NT, int SLOTS, int V>
+__device__ __forceinline__ void block_sum(Part<NT, SLOTS> (&v)[V], float (&out)[V], float* red2,
+                                          int& phase) {
   if (NT == kVirt) {
+    float* red = red2 + phase * kRed;
+    phase ^= 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < V; ++k) {
@@ -66,27 +78,37 @@ __device__ __forceinline__ void block_sum(Part<NT> (&v)[V], float (&out)[V], flo
       for (int w = 0; w < kVirt / 32; ++w) s += red[w * V + k];
       out[k] = s;
     }
-    __syncthreads();
   } else {
 #pragma unroll
     for (int k = 0; k < V; ++k) {
       float s = 0.f;
 #pragma unroll
-      for (int w = 0; w < kSlots; ++w) s += butterfly(v[k].p[w]);
+      for (int w = 0; w < SLOTS; ++w) s += butterfly(v[k].p[w]);
+      for (int w = SLOTS; w < kVirt / 32; ++w) s += 0.f;
       out[k] = s;
     }
   }
 }
 
-// NT = 256 for any seed up to 2048 variables; NT = 32 for seeds of at most
-// 256 variables (IK), same numerics.
-template <int NT>
+__device__ __forceinline__ void cp_async4(float* dst_smem, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// One CTA per seed; NT = 256 for seeds of 257..2048 variables, NT = 32 for
+// seeds of at most 256 (same numerics); SLOTS = ceil(n_max / NT).
+template <int NT, int SLOTS>
 __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
   static_assert(NT == 32 || NT == kVirt, "NT");
+  static_assert(NT * SLOTS <= kMaxN && (NT == 32 ? SLOTS <= kSlots : true), "SLOTS");
+  // line-search candidates and their gradients stay in registers when few
+  constexpr bool kHold = SLOTS <= 2;
+  constexpr int kHA = kHold ? CR_MAX_ALPHA : 1;
   extern __shared__ __align__(16) float osm[];
-  __shared__ float red[(kVirt / 32) * (CR_MAX_ALPHA + 1)];
+  __shared__ float red[2 * kRed];
   __shared__ float sh_rho[CR_MAX_HISTORY];
   __shared__ float sh_alpha[CR_MAX_HISTORY];
+  int phase = 0;
 
   const int tid = threadIdx.x;
   const int D = a.dof, m = a.prm.history, na = a.prm.n_alpha;
@@ -115,30 +137,67 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
     float* dir = st.dir + vo;
     float* cand = st.cand + (long long)vo * na;
     float* cgrad = st.cand_grad + (long long)vo * na;
-    __syncthreads();
+    float* hs = osm;                  // [m][n] s ring, slots as in device memory
+    float* hy = osm + (size_t)m * n;  // [m][n]
+    float* s_g = st.s + (long long)vo * m;
+    float* y_g = st.y + (long long)vo * m;
+    float* rho_g = st.rho + b * m;
+    __syncthreads();  // the previous seed is done with shared memory
+
+    // ---- every load that does not depend on the line-search choice, all in
+    // flight together: the history ring straight into shared memory, the
+    // iterate, previous iterate, direction and candidate gradients
+    if (a.do_propose) {
+      const int mn = m * n;
+      for (int k = tid; k < mn; k += NT) {
+        cp_async4(hs + k, s_g + k);
+        cp_async4(hy + k, y_g + k);
+      }
+      if (tid < m) sh_rho[tid] = rho_g[tid];
+    }
+    float xr[SLOTS], gr[SLOTS], dr[SLOTS], xpr[SLOTS], gpr[SLOTS];
+    float hc[kHA][SLOTS], hg[kHA][SLOTS];
+#pragma unroll
+    for (int e = 0; e < SLOTS; ++e) {
+      const int k = tid + NT * e;
+      const bool ok = k < n;
+      xr[e] = ok ? x[k] : 0.f;
+      gr[e] = ok ? g[k] : 0.f;
+      dr[e] = ok && a.do_select ? dir[k] : 0.f;
+      xpr[e] = ok && a.do_propose ? xp[k] : 0.f;
+      gpr[e] = ok && a.do_propose ? gp[k] : 0.f;
+      if (kHold && a.do_select) {
+#pragma unroll
+        for (int l = 0; l < kHA; ++l) {
+          hc[l][e] = ok && l < na ? cand[(long long)l * n + k] : 0.f;
+          hg[l][e] = ok && l < na ? cgrad[(long long)l * n + k] : 0.f;
+        }
+      }
+    }
 
     // ---------------- line-search selection (Alg. 1) ----------------
     if (a.do_select) {
-      Part<NT> v[CR_MAX_ALPHA + 1];
+      Part<NT, SLOTS> v[CR_MAX_ALPHA + 1];
 #pragma unroll
       for (int l = 0; l <= CR_MAX_ALPHA; ++l) v[l].zero();
 #pragma unroll
-      for (int e = 0; e < kSlots; ++e) {
+      for (int e = 0; e < SLOTS; ++e) {
         const int k = tid + NT * e;
         if (k < n) {
-          const float dk = dir[k];
-          v[0].fma(e, g[k], dk);
+          v[0].fma(e, gr[e], dr[e]);
 #pragma unroll
           for (int l = 0; l < CR_MAX_ALPHA; ++l)
-            if (l < na) v[1 + l].fma(e, cgrad[(long long)l * n + k], dk);
+            if (l < na) v[1 + l].fma(e, kHold ? hg[kHold ? l : 0][e] : cgrad[(long long)l * n + k], dr[e]);
         }
       }
       float tot[CR_MAX_ALPHA + 1];
-      block_sum<NT, CR_MAX_ALPHA + 1>(v, tot, red);
+      block_sum<NT, SLOTS, CR_MAX_ALPHA + 1>(v, tot, red, phase);
       const float c0 = st.c[b];
       const float gd0 = tot[0];
       int idx = 0;
-      for (int l = 0; l < na; ++l) {
+#pragma unroll
+      for (int l = 0; l < CR_MAX_ALPHA; ++l) {
+        if (l >= na) break;
         const float cl = st.cand_cost[b * na + l];
         bool ok = cl <= c0 + a.prm.armijo_c1 * a.prm.alpha[l] * gd0;
         if (a.prm.flags & CR_WOLFE) {
@@ -153,12 +212,27 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
       const float cnew = st.cand_cost[b * na + idx];
       const bool better = cnew < st.best_c[b];  // NaN never improves the best
 #pragma unroll
-      for (int e = 0; e < kSlots; ++e) {
+      for (int e = 0; e < SLOTS; ++e) {
         const int k = tid + NT * e;
         if (k < n) {
-          const float xv = cand[(long long)idx * n + k];
+          float xv, gv;
+          if (kHold) {
+            xv = hc[0][e];
+            gv = hg[0][e];
+#pragma unroll
+            for (int l = 1; l < kHA; ++l)
+              if (l == idx) {
+                xv = hc[l][e];
+                gv = hg[l][e];
+              }
+          } else {
+            xv = cand[(long long)idx * n + k];
+            gv = cgrad[(long long)idx * n + k];
+          }
+          xr[e] = xv;
+          gr[e] = gv;
           x[k] = xv;
-          g[k] = cgrad[(long long)idx * n + k];
+          g[k] = gv;
           if (better) st.best_x[vo + k] = xv;
         }
       }
@@ -173,77 +247,68 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
       }
     }
     if (a.init_best) {
-      for (int k = tid; k < n; k += NT) st.best_x[vo + k] = x[k];
+#pragma unroll
+      for (int e = 0; e < SLOTS; ++e) {
+        const int k = tid + NT * e;
+        if (k < n) st.best_x[vo + k] = xr[e];
+      }
       if (tid == 0) st.best_c[b] = st.c[b];
     }
 
     // ---------------- L-BFGS step (App. A.7) ----------------
     if (a.do_propose) {
-      float* hs = osm;                  // [m][n] s pairs, physical slots
-      float* hy = osm + (size_t)m * n;  // [m][n]
-      float* s_g = st.s + (long long)vo * m;
-      float* y_g = st.y + (long long)vo * m;
-      float* rho_g = st.rho + b * m;
-      for (int k = tid; k < m * n; k += NT) {
-        hs[k] = s_g[k];
-        hy[k] = y_g[k];
-      }
-      if (tid < m) sh_rho[tid] = rho_g[tid];
       const int it = st.iter[b];
-      float xr[kSlots], gr[kSlots];
-#pragma unroll
-      for (int e = 0; e < kSlots; ++e) {
-        const int k = tid + NT * e;
-        xr[e] = k < n ? x[k] : 0.f;
-        gr[e] = k < n ? g[k] : 0.f;
-      }
-      __syncthreads();
-      int shift = 0;  // logical pair i (0 = oldest) lives in physical slot (i + shift) % m
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      __syncthreads();  // the ring and rho are in shared memory
+      // logical pair i (0 = oldest) lives in slot (i + shift) % m; with
+      // it > 0 this call appends pair number it, in slot (it - 1) % m
+      int shift = 0;
       if (it > 0) {
-        // the newest pair overwrites the oldest slot (physical 0)
-        float sv[kSlots], yv[kSlots];
-        Part<NT> ys[1];
+        const int w = (it - 1) % m;
+        float sv[SLOTS], yv[SLOTS];
+        Part<NT, SLOTS> ys[1];
         ys[0].zero();
 #pragma unroll
-        for (int e = 0; e < kSlots; ++e) {
+        for (int e = 0; e < SLOTS; ++e) {
           const int k = tid + NT * e;
-          sv[e] = k < n ? xr[e] - xp[k] : 0.f;
-          yv[e] = k < n ? gr[e] - gp[k] : 0.f;
+          sv[e] = k < n ? xr[e] - xpr[e] : 0.f;
+          yv[e] = k < n ? gr[e] - gpr[e] : 0.f;
           if (k < n) ys[0].fma(e, yv[e], sv[e]);
         }
         float yst[1];
-        block_sum<NT, 1>(ys, yst, red);
+        block_sum<NT, SLOTS, 1>(ys, yst, red, phase);
 #pragma unroll
-        for (int e = 0; e < kSlots; ++e) {
+        for (int e = 0; e < SLOTS; ++e) {
           const int k = tid + NT * e;
           if (k < n) {
-            hs[k] = sv[e];
-            hy[k] = yv[e];
+            hs[(long long)w * n + k] = sv[e];
+            hy[(long long)w * n + k] = yv[e];
+            s_g[(long long)w * n + k] = sv[e];
+            y_g[(long long)w * n + k] = yv[e];
           }
         }
-        if (tid == 0) sh_rho[0] = yst[0] > 1e-8f ? 1.f / yst[0] : 0.f;
-        shift = 1;
+        if (tid == 0) {
+          const float r = yst[0] > 1e-8f ? 1.f / yst[0] : 0.f;
+          sh_rho[w] = r;
+          rho_g[w] = r;
+        }
+        shift = it % m;
         __syncthreads();
-        // write back newest-last
-        for (int i = 0; i < m; ++i) {
-          const int p = (i + shift) % m;
-          for (int k = tid; k < n; k += NT) {
-            s_g[(long long)i * n + k] = hs[(long long)p * n + k];
-            y_g[(long long)i * n + k] = hy[(long long)p * n + k];
-          }
-        }
-        if (tid < m) rho_g[tid] = sh_rho[(tid + shift) % m];
       }
-      for (int k = tid; k < n; k += NT) {
-        xp[k] = x[k];
-        gp[k] = g[k];
+#pragma unroll
+      for (int e = 0; e < SLOTS; ++e) {
+        const int k = tid + NT * e;
+        if (k < n) {
+          xp[k] = xr[e];
+          gp[k] = gr[e];
+        }
       }
       if (tid == 0) st.iter[b] = it + 1;
 
       // two-loop recursion: q = g; newest to oldest
-      float q[kSlots];
+      float q[SLOTS];
 #pragma unroll
-      for (int e = 0; e < kSlots; ++e) q[e] = gr[e];
+      for (int e = 0; e < SLOTS; ++e) q[e] = gr[e];
       for (int i = m - 1; i >= 0; --i) {
         const int p = (i + shift) % m;
         const float rho = sh_rho[p];
@@ -251,19 +316,19 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
           if (tid == 0) sh_alpha[i] = 0.f;
           continue;
         }
-        Part<NT> d[1];
+        Part<NT, SLOTS> d[1];
         d[0].zero();
 #pragma unroll
-        for (int e = 0; e < kSlots; ++e) {
+        for (int e = 0; e < SLOTS; ++e) {
           const int k = tid + NT * e;
           if (k < n) d[0].fma(e, hs[(long long)p * n + k], q[e]);
         }
         float dt[1];
-        block_sum<NT, 1>(d, dt, red);
+        block_sum<NT, SLOTS, 1>(d, dt, red, phase);
         const float al = rho * dt[0];
         if (tid == 0) sh_alpha[i] = al;
 #pragma unroll
-        for (int e = 0; e < kSlots; ++e) {
+        for (int e = 0; e < SLOTS; ++e) {
           const int k = tid + NT * e;
           if (k < n) q[e] = fmaf(-al, hy[(long long)p * n + k], q[e]);
         }
@@ -273,11 +338,11 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
       for (int i = m - 1; i >= 0; --i) {
         const int p = (i + shift) % m;
         if (sh_rho[p] > 0.f) {
-          Part<NT> d[2];
+          Part<NT, SLOTS> d[2];
           d[0].zero();
           d[1].zero();
 #pragma unroll
-          for (int e = 0; e < kSlots; ++e) {
+          for (int e = 0; e < SLOTS; ++e) {
             const int k = tid + NT * e;
             if (k < n) {
               const float sv = hs[(long long)p * n + k], yv = hy[(long long)p * n + k];
@@ -286,37 +351,37 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
             }
           }
           float dt[2];
-          block_sum<NT, 2>(d, dt, red);
+          block_sum<NT, SLOTS, 2>(d, dt, red, phase);
           gamma = dt[0] / dt[1];
           break;
         }
       }
 #pragma unroll
-      for (int e = 0; e < kSlots; ++e) q[e] *= gamma;
+      for (int e = 0; e < SLOTS; ++e) q[e] *= gamma;
       __syncthreads();  // sh_alpha visible
       for (int i = 0; i < m; ++i) {
         const int p = (i + shift) % m;
         const float rho = sh_rho[p];
         if (rho == 0.f) continue;
-        Part<NT> d[1];
+        Part<NT, SLOTS> d[1];
         d[0].zero();
 #pragma unroll
-        for (int e = 0; e < kSlots; ++e) {
+        for (int e = 0; e < SLOTS; ++e) {
           const int k = tid + NT * e;
           if (k < n) d[0].fma(e, hy[(long long)p * n + k], q[e]);
         }
         float dt[1];
-        block_sum<NT, 1>(d, dt, red);
+        block_sum<NT, SLOTS, 1>(d, dt, red, phase);
         const float coef = sh_alpha[i] - rho * dt[0];
 #pragma unroll
-        for (int e = 0; e < kSlots; ++e) {
+        for (int e = 0; e < SLOTS; ++e) {
           const int k = tid + NT * e;
           if (k < n) q[e] = fmaf(hs[(long long)p * n + k], coef, q[e]);
         }
       }
       // direction and the clipped candidates of Alg. 1
 #pragma unroll
-      for (int e = 0; e < kSlots; ++e) {
+      for (int e = 0; e < SLOTS; ++e) {
         const int k = tid + NT * e;
         if (k < n) {
           const float dk = -q[e];
@@ -337,7 +402,7 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
 // The largest dynamic shared memory any launch may ask for is set once per
 // kernel and device (never lowered), so launches captured in a graph stay
 // valid whatever is launched later.
-template <int NT>
+template <int NT, int SLOTS>
 cudaError_t allow_opt_smem() {
   static unsigned done = 0;  // bit per device
   int dev = 0;
@@ -346,9 +411,18 @@ cudaError_t allow_opt_smem() {
   if (done & bit) return cudaSuccess;
   // 200 KB covers every accepted history * horizon * dof and stays below the
   // opt-in limit together with the kernel's static shared memory
-  cudaError_t e = cudaFuncSetAttribute(k_opt<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_opt<NT, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess) done |= bit;
   return e;
+}
+
+template <int NT, int SLOTS>
+cudaError_t launch_opt_as(const OptArgs& a, int smem, cudaStream_t stream) {
+  cudaError_t e = allow_opt_smem<NT, SLOTS>();
+  if (e != cudaSuccess) return e;
+  k_opt<NT, SLOTS><<<a.n_seeds, NT, smem, stream>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -359,16 +433,13 @@ cudaError_t launch_opt(const OptArgs& a, int n_max, cudaStream_t stream) {
   if (a.n_seeds <= 0) return cudaSuccess;
   if (n_max > kMaxN) return cudaErrorInvalidValue;
   const int smem = a.do_propose ? opt_smem_bytes(a.prm.history, n_max) : 0;
-  if (n_max <= kVirt) {
-    cudaError_t e = allow_opt_smem<32>();
-    if (e != cudaSuccess) return e;
-    k_opt<32><<<a.n_seeds, 32, smem, stream>>>(a);
-  } else {
-    cudaError_t e = allow_opt_smem<kVirt>();
-    if (e != cudaSuccess) return e;
-    k_opt<kVirt><<<a.n_seeds, kVirt, smem, stream>>>(a);
-  }
-  return cudaGetLastError();
+  if (n_max <= 32) return launch_opt_as<32, 1>(a, smem, stream);
+  if (n_max <= 64) return launch_opt_as<32, 2>(a, smem, stream);
+  if (n_max <= 128) return launch_opt_as<32, 4>(a, smem, stream);
+  if (n_max <= kVirt) return launch_opt_as<32, 8>(a, smem, stream);
+  if (n_max <= 2 * kVirt) return launch_opt_as<kVirt, 2>(a, smem, stream);
+  if (n_max <= 4 * kVirt) return launch_opt_as<kVirt, 4>(a, smem, stream);
+  return launch_opt_as<kVirt, 8>(a, smem, stream);
 }
 
 }  // namespace crgb

@@ -44,15 +44,22 @@ def _history_state(n, m, k_steps, seed):
     return st
 
 
+def _ring(a, it):
+    """Oracle history (oldest first, newest last) as the device ring holds it
+    when iter = it: logical pair i in slot (it - 1 + i) mod m."""
+    return np.roll(a, (int(it) - 1) % a.shape[0], axis=0)
+
+
 def _load(buf, b, st):
     buf.x[b] = torch.tensor(st.x, dtype=torch.float32)
     buf.g[b] = torch.tensor(st.g, dtype=torch.float32)
     buf.x_prev[b] = torch.tensor(st.x_prev, dtype=torch.float32)
     buf.g_prev[b] = torch.tensor(st.g_prev, dtype=torch.float32)
-    buf.s[b] = torch.tensor(st.s, dtype=torch.float32)
-    buf.y[b] = torch.tensor(st.y, dtype=torch.float32)
-    buf.rho[b] = torch.tensor(st.rho, dtype=torch.float32)
-    buf.iter[b] = int(st.iter[0])
+    it = int(st.iter[0])
+    buf.s[b] = torch.tensor(_ring(st.s, it), dtype=torch.float32)
+    buf.y[b] = torch.tensor(_ring(st.y, it), dtype=torch.float32)
+    buf.rho[b] = torch.tensor(_ring(st.rho, it), dtype=torch.float32)
+    buf.iter[b] = it
 
 
 @pytest.mark.parametrize("H,m,k_steps", [(32, 6, 0), (32, 6, 1), (32, 6, 3), (48, 6, 9),
@@ -83,9 +90,10 @@ def test_propose_matches_oracle(H, m, k_steps):
         assert np.linalg.norm(dg - d) <= 1e-3 * np.linalg.norm(d) + 1e-7, (b, np.linalg.norm(dg - d))
         cg = buf.cand[b].cpu().numpy()
         assert np.abs(cg - cand).max() <= 1e-3 * np.abs(d).max() + 1e-6
-        np.testing.assert_allclose(buf.s[b].cpu().numpy(), st.s, atol=1e-6)
-        np.testing.assert_allclose(buf.y[b].cpu().numpy(), st.y, atol=1e-5, rtol=1e-5)
-        np.testing.assert_allclose(buf.rho[b].cpu().numpy(), st.rho, rtol=1e-4)
+        it = int(st.iter[0])
+        np.testing.assert_allclose(buf.s[b].cpu().numpy(), _ring(st.s, it), atol=1e-6)
+        np.testing.assert_allclose(buf.y[b].cpu().numpy(), _ring(st.y, it), atol=1e-5, rtol=1e-5)
+        np.testing.assert_allclose(buf.rho[b].cpu().numpy(), _ring(st.rho, it), rtol=1e-4)
         np.testing.assert_array_equal(buf.x_prev[b].cpu().numpy(), st.x.astype(np.float32))
         assert int(buf.iter[b]) == int(st.iter[0])
 
