@@ -17,6 +17,32 @@ constexpr int kMaxHorizon = 128;
 constexpr int kBoxChunk = 64;  // boxes staged in shared memory at a time
 constexpr int kEvalBlock = 512; // threads of an evaluation CTA
 
+// Programmatic dependent launch: the evaluation and optimiser kernels are
+// launched so that the next one may start while the previous one finishes.
+// Each waits (griddepcontrol.wait) before it touches anything the previous
+// grid writes, then lets its own dependent start (launch_dependents); without
+// a programmatic predecessor the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename Kern, typename... Args>
+inline cudaError_t launch_pdl(Kern kern, int grid, int block, size_t smem, cudaStream_t stream,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Robot as the kernels see it (device pointers into one allocation).
 struct RobotView {
   int dof, n_spheres, n_pairs, n_groups;
@@ -143,6 +169,9 @@ struct OptArgs {
   int do_propose;
   int init_best;       // first call after the initial evaluation: best := current
   int* reset_queue;    // the next evaluation's work counter, zeroed here (or nullptr)
+  int early_loads;     // the previous grid is a candidate evaluation, which writes only
+                       // cand_cost / cand_grad / cand_cfree: everything else may be
+                       // loaded before that grid has finished
 };
 
 // Per-problem output pointers of the finishing kernel (runtime.cu).

@@ -260,6 +260,10 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   for (int k = tid; k < P; k += nthr) s_pairs[k] = a.rb.pairs[k];
   for (int k = tid; k < G; k += nthr) s_grp[k] = a.rb.groups[k];
   for (int k = tid; k < D; k += nthr) s_axis[k] = a.rb.axis[k];
+  // the robot is constant; trajectories, the work counter and the outputs
+  // belong to the previous grid until it has finished
+  pdl_wait();
+  pdl_launch_dependents();
 
   const int n_tiles = a.problems ? a.n_tiles
                                  : (a.prob0.n_traj + a.traj_per_tile - 1) / a.traj_per_tile;
@@ -1008,11 +1012,8 @@ cudaError_t launch_eval(const EvalArgs& a_in, int grid, int block, cudaStream_t 
   a.store_x = sx ? 1 : 0;
   cudaError_t e = allow_eval_smem();
   if (e != cudaSuccess) return e;
-  if (two)
-    k_eval<2><<<grid, block, smem, stream>>>(a);
-  else
-    k_eval<1><<<grid, block, smem, stream>>>(a);
-  return cudaGetLastError();
+  return two ? launch_pdl(k_eval<2>, grid, block, smem, stream, a)
+             : launch_pdl(k_eval<1>, grid, block, smem, stream, a);
 }
 
 cudaError_t launch_fk(const RobotView& rb, const float* theta, int n, float* spheres, float* ee,

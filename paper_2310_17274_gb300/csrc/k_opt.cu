@@ -113,10 +113,6 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
   const int tid = threadIdx.x;
   const int D = a.dof, m = a.prm.history, na = a.prm.n_alpha;
   const cr_opt_state& st = a.st;
-  // the evaluation that ran before this launch is complete: its work counter
-  // can start over for the next one (saves a memset node per iteration)
-  if (a.reset_queue && blockIdx.x == 0 && tid == 0) *a.reset_queue = 0;
-
   for (int bt = blockIdx.x; bt < a.n_seeds; bt += gridDim.x) {
     // b: the seed's index in the per-seed arrays (the table may list a subset)
     int n, vo, b;
@@ -146,7 +142,10 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
 
     // ---- every load that does not depend on the line-search choice, all in
     // flight together: the history ring straight into shared memory, the
-    // iterate, previous iterate, direction and candidate gradients
+    // iterate, previous iterate, direction and candidates; before the
+    // previous grid has finished only when that grid cannot have written them
+    const bool early = a.early_loads && a.do_select;
+    if (!early) pdl_wait();
     if (a.do_propose) {
       const int mn = m * n;
       for (int k = tid; k < mn; k += NT) {
@@ -168,10 +167,23 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
       gpr[e] = ok && a.do_propose ? gp[k] : 0.f;
       if (kHold && a.do_select) {
 #pragma unroll
-        for (int l = 0; l < kHA; ++l) {
-          hc[l][e] = ok && l < na ? cand[(long long)l * n + k] : 0.f;
-          hg[l][e] = ok && l < na ? cgrad[(long long)l * n + k] : 0.f;
-        }
+        for (int l = 0; l < kHA; ++l) hc[l][e] = ok && l < na ? cand[(long long)l * n + k] : 0.f;
+      }
+    }
+    // the evaluation's own outputs are read only after it is done
+    if (early) pdl_wait();
+    if (bt == blockIdx.x) {
+      pdl_launch_dependents();
+      // the evaluation that ran before this launch is complete: its work
+      // counter can start over for the next one (saves a memset node)
+      if (a.reset_queue && blockIdx.x == 0 && tid == 0) *a.reset_queue = 0;
+    }
+    if (kHold && a.do_select) {
+#pragma unroll
+      for (int e = 0; e < SLOTS; ++e) {
+        const int k = tid + NT * e;
+#pragma unroll
+        for (int l = 0; l < kHA; ++l) hg[l][e] = k < n && l < na ? cgrad[(long long)l * n + k] : 0.f;
       }
     }
 
@@ -421,8 +433,7 @@ template <int NT, int SLOTS>
 cudaError_t launch_opt_as(const OptArgs& a, int smem, cudaStream_t stream) {
   cudaError_t e = allow_opt_smem<NT, SLOTS>();
   if (e != cudaSuccess) return e;
-  k_opt<NT, SLOTS><<<a.n_seeds, NT, smem, stream>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_opt<NT, SLOTS>, a.n_seeds, NT, (size_t)smem, stream, a);
 }
 
 }  // namespace

@@ -369,6 +369,7 @@ cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* p
     if (rs != CR_OK) return rs;
     o.do_select = 1;
     o.do_propose = it + 1 < iters;
+    o.early_loads = 1;  // follows the candidate evaluation directly
     RT_CUDA(launch_opt(o, pl.n_max, s));
   }
   RT_CUDA(launch_finish((const ResultView*)(tab + pl.o_res), pl.P, st.best_x, st.best_c,
