@@ -154,12 +154,17 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
       }
       if (tid < m) sh_rho[tid] = rho_g[tid];
     }
-    float xr[SLOTS], gr[SLOTS], dr[SLOTS], xpr[SLOTS], gpr[SLOTS];
+    float xr[SLOTS], gr[SLOTS], dr[SLOTS], xpr[SLOTS], gpr[SLOTS], lo[SLOTS], hi[SLOTS];
     float hc[kHA][SLOTS], hg[kHA][SLOTS];
+    const int it = a.do_propose ? st.iter[b] : 0;
+    const float c_cur = a.do_select ? st.c[b] : 0.f;
+    const float c_best = a.do_select ? st.best_c[b] : 0.f;
 #pragma unroll
     for (int e = 0; e < SLOTS; ++e) {
       const int k = tid + NT * e;
       const bool ok = k < n;
+      lo[e] = ok && a.do_propose ? a.q_lo[k % D] : 0.f;
+      hi[e] = ok && a.do_propose ? a.q_hi[k % D] : 0.f;
       xr[e] = ok ? x[k] : 0.f;
       gr[e] = ok ? g[k] : 0.f;
       dr[e] = ok && a.do_select ? dir[k] : 0.f;
@@ -186,6 +191,9 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
         for (int l = 0; l < kHA; ++l) hg[l][e] = k < n && l < na ? cgrad[(long long)l * n + k] : 0.f;
       }
     }
+    float ccost[CR_MAX_ALPHA];  // candidate costs, every thread (same addresses)
+#pragma unroll
+    for (int l = 0; l < CR_MAX_ALPHA; ++l) ccost[l] = a.do_select && l < na ? st.cand_cost[b * na + l] : 0.f;
 
     // ---------------- line-search selection (Alg. 1) ----------------
     if (a.do_select) {
@@ -204,13 +212,14 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
       }
       float tot[CR_MAX_ALPHA + 1];
       block_sum<NT, SLOTS, CR_MAX_ALPHA + 1>(v, tot, red, phase);
-      const float c0 = st.c[b];
+      const float c0 = c_cur;
       const float gd0 = tot[0];
       int idx = 0;
+      float cnew = ccost[0];
 #pragma unroll
       for (int l = 0; l < CR_MAX_ALPHA; ++l) {
         if (l >= na) break;
-        const float cl = st.cand_cost[b * na + l];
+        const float cl = ccost[l];
         bool ok = cl <= c0 + a.prm.armijo_c1 * a.prm.alpha[l] * gd0;
         if (a.prm.flags & CR_WOLFE) {
           const float gld = tot[1 + l];
@@ -219,10 +228,12 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
           else
             ok = ok && gld >= a.prm.wolfe_c2 * gd0;
         }
-        if (ok) idx = l;  // largest passing index; 0 when none passes
+        if (ok) {  // largest passing index; 0 when none passes
+          idx = l;
+          cnew = cl;
+        }
       }
-      const float cnew = st.cand_cost[b * na + idx];
-      const bool better = cnew < st.best_c[b];  // NaN never improves the best
+      const bool better = cnew < c_best;  // NaN never improves the best
 #pragma unroll
       for (int e = 0; e < SLOTS; ++e) {
         const int k = tid + NT * e;
@@ -248,7 +259,6 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
           if (better) st.best_x[vo + k] = xv;
         }
       }
-      __syncthreads();  // every thread has read c[b] and best_c[b]
       if (tid == 0) {
         st.c[b] = cnew;
         st.ls_index[b] = idx;
@@ -269,7 +279,6 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
 
     // ---------------- L-BFGS step (App. A.7) ----------------
     if (a.do_propose) {
-      const int it = st.iter[b];
       asm volatile("cp.async.wait_all;\n" ::: "memory");
       __syncthreads();  // the ring and rho are in shared memory
       // logical pair i (0 = oldest) lives in slot (i + shift) % m; with
@@ -398,11 +407,9 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
         if (k < n) {
           const float dk = -q[e];
           dir[k] = dk;
-          const int j = k % D;
-          const float lo = a.q_lo[j], hi = a.q_hi[j];
           for (int l = 0; l < na; ++l) {
             float v = fmaf(a.prm.alpha[l], dk, xr[e]);
-            v = fminf(fmaxf(v, lo), hi);
+            v = fminf(fmaxf(v, lo[e]), hi[e]);
             cand[(long long)l * n + k] = v;
           }
         }
