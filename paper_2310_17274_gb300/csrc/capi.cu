@@ -255,7 +255,9 @@ cr_status cr_world_create(const cr_world_desc* d, cr_world** out) {
       double t = -(R[0 * 3 + a] * p[0] + R[1 * 3 + a] * p[1] + R[2 * 3 + a] * p[2]);
       r[a] = make_float4((float)R[0 * 3 + a], (float)R[1 * 3 + a], (float)R[2 * 3 + a], (float)t);
     }
-    rows[k].h = make_float4(h[0], h[1], h[2], std::sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]));
+    const float hn = (float)std::sqrt((double)h[0] * h[0] + (double)h[1] * h[1] + (double)h[2] * h[2]);
+    rows[k].h = make_float4(h[0], h[1], h[2], hn);
+    rows[k].c = make_float4(p[0], p[1], p[2], hn);
   }
   BoxRows* dev = nullptr;
   cudaError_t e = cudaMalloc(&dev, rows.size() * sizeof(BoxRows));

@@ -60,10 +60,11 @@ struct RobotView {
   const int4* groups;       // [G] (link a, link b, first pair, pair count)
 };
 
-// One box packed as four float4 rows: (R^T row k, t_k) for k = 0..2 so that
-// u = R^T x + t is the point in the box frame, then (half extents, |h|).
+// One box packed as five float4 rows: (R^T row k, t_k) for k = 0..2 so that
+// u = R^T x + t is the point in the box frame, then (half extents, |h|), then
+// (centre in the world frame, |h|), the box's bounding sphere.
 struct BoxRows {
-  float4 r0, r1, r2, h;
+  float4 r0, r1, r2, h, c;
 };
 
 // One problem of a batch.
@@ -141,7 +142,7 @@ struct EvalSmem {
     off_sta = take(max_states * 4);
     off_gth = take(max_states * dof * 4);
     off_wsph = take(store_x ? 0 : n_warps * M * 16);
-    off_box = take(kBoxChunk * 64);
+    off_box = take(kBoxChunk * (int)sizeof(BoxRows));
     off_ee = take(max_traj * 48);
     // stencil samples of a tile: nt (H + 1) <= max_states + max_traj
     const int n_samples = (max_states + max_traj) * dof;

@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   __shared__ ProblemView s_prob;
   __shared__ int s_axis[kMaxDof];
   __shared__ int s_next;
+  __shared__ int s_nlist;
 
   const int D = a.rb.dof, M = a.rb.n_spheres, P = a.rb.n_pairs, G = a.rb.n_groups;
   const int GW = (G + 31) / 32;
@@ -230,12 +231,12 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   const int MW = (M + 31) / 32;
   float4* s_rho = reinterpret_cast<float4*>(smem + L.off_rho);
   uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem + L.off_mask);  // 2 words per (state, link)
-  uint32_t* s_gmask = reinterpret_cast<uint32_t*>(smem + L.off_gmask);
   float* s_stw = reinterpret_cast<float*>(smem + L.off_stw);
   float* s_sts = reinterpret_cast<float*>(smem + L.off_sts);
   int* s_sta = reinterpret_cast<int*>(smem + L.off_sta);
-  float* s_gth = reinterpret_cast<float*>(smem + L.off_gth);
+  uint32_t* s_gmask = reinterpret_cast<uint32_t*>(smem + L.off_gmask);
   float4* s_wsph = reinterpret_cast<float4*>(smem + L.off_wsph);
+  float* s_gth = reinterpret_cast<float*>(smem + L.off_gth);
   BoxRows* s_box = reinterpret_cast<BoxRows*>(smem + L.off_box);
   float4* s_ee = reinterpret_cast<float4*>(smem + L.off_ee);
   float* s_sten = reinterpret_cast<float*>(smem + L.off_sten);
@@ -244,6 +245,9 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   float* s_sm = reinterpret_cast<float*>(smem + L.off_sm);
   float* s_goal = reinterpret_cast<float*>(smem + L.off_goal);
   int* s_free = reinterpret_cast<int*>(smem + L.off_free);
+  // the sweep's work list lives in the stencil region, unused until later
+  uint32_t* s_list = reinterpret_cast<uint32_t*>(smem + L.off_sten);
+  const int list_cap = (L.off_pb - L.off_sten) / 12;
 
   // robot model, once per CTA
   for (int k = tid; k < (D + 1) * 12; k += nthr) s_fix[k] = a.rb.fixed_tf[k];
@@ -465,7 +469,9 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
         {
           const float4* src = reinterpret_cast<const float4*>(s_prob.boxes + c0);
           float4* dst = reinterpret_cast<float4*>(s_box);
-          for (int k = tid; k < kc * 4; k += nthr) dst[k] = src[k];
+          constexpr int kRow = (int)(sizeof(BoxRows) / 16);
+          for (int k = tid; k < kc * kRow; k += nthr) dst[k] = src[k];
+          if (tid == 0) s_nlist = 0;
         }
         __syncthreads();
         // (1) per (state, link): bitmask of the boxes within reach
@@ -477,6 +483,10 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
 #pragma unroll 4
             for (int kk = 0; kk < kc; ++kk) {
               const BoxRows& b = s_box[kk];
+              // bounding spheres apart: the box test below cannot pass
+              const float cx = lc.x - b.c.x, cy = lc.y - b.c.y, cz = lc.z - b.c.z;
+              const float rb = (lc.w + b.c.w) * 1.0001f + 1e-6f;
+              if (fmaf(cx, cx, fmaf(cy, cy, cz * cz)) >= rb * rb) continue;
               const float ux = fmaf(b.r0.x, lc.x, fmaf(b.r0.y, lc.y, fmaf(b.r0.z, lc.z, b.r0.w)));
               const float uy = fmaf(b.r1.x, lc.x, fmaf(b.r1.y, lc.y, fmaf(b.r1.z, lc.z, b.r1.w)));
               const float uz = fmaf(b.r2.x, lc.x, fmaf(b.r2.y, lc.y, fmaf(b.r2.z, lc.z, b.r2.w)));
@@ -490,34 +500,11 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
           s_mask[2 * k + 1] = (uint32_t)(m >> 32);
         }
         __syncthreads();
-        // (2) per (state, sphere): the boxes of its link's mask in box order
-        for (int k = tid; k < S * M; k += nthr) {
+        // (2) the sweep of a (state, sphere) over the boxes in mask m, in box order
+        auto sweep_item = [&](int k, unsigned long long m) {
           const int sg = k / M, i = k % M;
-          const float rad = s_sph[i].w;
-          if (rad < 0.f) continue;
-          const int sl0 = sg * D + s_link[i];
-          unsigned long long m0 = (unsigned long long)s_mask[2 * sl0] | ((unsigned long long)s_mask[2 * sl0 + 1] << 32);
-          if (!m0) continue;
           const int r = sg / H;
-          // boxes within the link-level bound of this sphere's reach first
-          unsigned long long m = 0ull;
-          {
-            const V3 xp = pos(slot(r, sg % H + 1), i);
-            const float tu = rad + s_lm[sg * D + s_link[i]];
-            while (m0) {
-              const int kk = __ffsll((long long)m0) - 1;
-              m0 &= m0 - 1ull;
-              const BoxRows& b = s_box[kk];
-              const float ux = fmaf(b.r0.x, xp.x, fmaf(b.r0.y, xp.y, fmaf(b.r0.z, xp.z, b.r0.w)));
-              const float uy = fmaf(b.r1.x, xp.x, fmaf(b.r1.y, xp.y, fmaf(b.r1.z, xp.z, b.r1.w)));
-              const float uz = fmaf(b.r2.x, xp.x, fmaf(b.r2.y, xp.y, fmaf(b.r2.z, xp.z, b.r2.w)));
-              const float mx = fmaxf(fabsf(ux) - b.h.x, 0.f);
-              const float my = fmaxf(fabsf(uy) - b.h.y, 0.f);
-              const float mz = fmaxf(fabsf(uz) - b.h.z, 0.f);
-              if (fmaf(mx, mx, fmaf(my, my, mz * mz)) < tu * tu) m |= 1ull << kk;
-            }
-          }
-          if (!m) continue;
+          const float rad = s_sph[i].w;
           const SphereMotion mo = motion(r, sg % H + 1, i);
           const V3 x1 = mo.x1;
           float4 acc4 = s_sg[k];
@@ -525,7 +512,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
           while (m) {
             const int kk = __ffsll((long long)m) - 1;
             m &= m - 1ull;
-            const BoxRows b = s_box[kk];
+            const BoxRows& b = s_box[kk];
             const float ux = fmaf(b.r0.x, x1.x, fmaf(b.r0.y, x1.y, fmaf(b.r0.z, x1.z, b.r0.w)));
             const float uy = fmaf(b.r1.x, x1.x, fmaf(b.r1.y, x1.y, fmaf(b.r1.z, x1.z, b.r1.w)));
             const float uz = fmaf(b.r2.x, x1.x, fmaf(b.r2.y, x1.y, fmaf(b.r2.z, x1.z, b.r2.w)));
@@ -566,6 +553,53 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
           }
           s_sg[k] = acc4;
           if (!clear) s_free[r] = 0;
+        };
+        // (2a) per (state, sphere): the boxes of its link's mask that are within
+        //      the link-level bound of the sphere; the few items with any go to a
+        //      list (inline when the list is full) so that (2b) runs them densely
+        for (int k = tid; k < S * M; k += nthr) {
+          const int sg = k / M, i = k % M;
+          const float rad = s_sph[i].w;
+          if (rad < 0.f) continue;
+          const int sl0 = sg * D + s_link[i];
+          unsigned long long m0 = (unsigned long long)s_mask[2 * sl0] | ((unsigned long long)s_mask[2 * sl0 + 1] << 32);
+          if (!m0) continue;
+          const int r = sg / H;
+          // boxes within the link-level bound of this sphere's reach first
+          unsigned long long m = 0ull;
+          {
+            const V3 xp = pos(slot(r, sg % H + 1), i);
+            const float tu = rad + s_lm[sg * D + s_link[i]];
+            while (m0) {
+              const int kk = __ffsll((long long)m0) - 1;
+              m0 &= m0 - 1ull;
+              const BoxRows& b = s_box[kk];
+              const float ux = fmaf(b.r0.x, xp.x, fmaf(b.r0.y, xp.y, fmaf(b.r0.z, xp.z, b.r0.w)));
+              const float uy = fmaf(b.r1.x, xp.x, fmaf(b.r1.y, xp.y, fmaf(b.r1.z, xp.z, b.r1.w)));
+              const float uz = fmaf(b.r2.x, xp.x, fmaf(b.r2.y, xp.y, fmaf(b.r2.z, xp.z, b.r2.w)));
+              const float mx = fmaxf(fabsf(ux) - b.h.x, 0.f);
+              const float my = fmaxf(fabsf(uy) - b.h.y, 0.f);
+              const float mz = fmaxf(fabsf(uz) - b.h.z, 0.f);
+              if (fmaf(mx, mx, fmaf(my, my, mz * mz)) < tu * tu) m |= 1ull << kk;
+            }
+          }
+          if (!m) continue;
+          const int e = atomicAdd(&s_nlist, 1);
+          if (e < list_cap) {
+            s_list[3 * e] = (uint32_t)k;
+            s_list[3 * e + 1] = (uint32_t)m;
+            s_list[3 * e + 2] = (uint32_t)(m >> 32);
+          } else {
+            sweep_item(k, m);
+          }
+        }
+        __syncthreads();
+        // (2b) the listed items, any thread: each item keeps its own box order
+        {
+          const int n_list = min(s_nlist, list_cap);
+          for (int e = tid; e < n_list; e += nthr)
+            sweep_item((int)s_list[3 * e],
+                       (unsigned long long)s_list[3 * e + 1] | ((unsigned long long)s_list[3 * e + 2] << 32));
         }
       }
     }
