@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   // the sweep's work list lives in the stencil region, unused until later
   uint32_t* s_list = reinterpret_cast<uint32_t*>(smem + L.off_sten);
   const int list_cap = (L.off_pb - L.off_sten) / 12;
+  const int bw_cap = (L.off_pb - L.off_sten) / 4;  // the backward pass's list, same region
 
   // robot model, once per CTA
   for (int k = tid; k < (D + 1) * 12; k += nthr) s_fix[k] = a.rb.fixed_tf[k];
@@ -691,27 +692,12 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     //     sweep gradient scaled by the speed, plus the speed's dependence on
     //     the neighbouring waypoints) and the self term; it replaces the sweep
     //     gradient in place (the sum S stays for the neighbours)
-    for (int k = tid; k < S * M; k += nthr) {
+    auto bw1_item = [&](int k) {
       const int sg = k / M, i = k % M;
       const int r = sg / H, t = sg % H + 1;
       const float4 c = s_sph[i];
       float wc = 0.f;
       V3 gx = v3(0.f, 0.f, 0.f);
-      const int parg0 = selfc ? s_sta[sg] : -1;
-      bool in_pair = false;
-      if (parg0 >= 0) {
-        const uint32_t pr = s_pairs[parg0];
-        in_pair = i == (int)(pr & 0xffffu) || i == (int)(pr >> 16);
-      }
-      {
-        // nothing reaches this sphere: its gradient and cost stay zero
-        const float4 own = s_sg[k];
-        const float Sm0 = (speed && t >= 2) ? s_sg[k - M].x : 0.f;
-        const float Sp0 = (speed && t + 1 <= H) ? s_sg[k + M].x : 0.f;
-        if (!in_pair && own.x == 0.f && own.y == 0.f && own.z == 0.f && own.w == 0.f && Sm0 == 0.f &&
-            Sp0 == 0.f)
-          continue;
-      }
       if (c.w >= 0.f) {
         const V3 x = pos(slot(r, t), i);
         if (K > 0) {
@@ -763,6 +749,37 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
       g3[3] = gx.z;
       if (wc != 0.f || gx.x != 0.f || gx.y != 0.f || gx.z != 0.f)
         atomicOr(&s_nz[sg * MW + i / 32], 1u << (i % 32));
+    };
+    // (1a) list the (state, sphere) items whose gradient can be non-zero:
+    //      nothing reaches the others, their gradient and cost stay zero
+    if (tid == 0) s_nlist = 0;
+    __syncthreads();
+    for (int k = tid; k < S * M; k += nthr) {
+      const int sg = k / M, i = k % M;
+      const int t = sg % H + 1;
+      const int parg0 = selfc ? s_sta[sg] : -1;
+      bool in_pair = false;
+      if (parg0 >= 0) {
+        const uint32_t pr = s_pairs[parg0];
+        in_pair = i == (int)(pr & 0xffffu) || i == (int)(pr >> 16);
+      }
+      const float4 own = s_sg[k];
+      const float Sm0 = (speed && t >= 2) ? s_sg[k - M].x : 0.f;
+      const float Sp0 = (speed && t + 1 <= H) ? s_sg[k + M].x : 0.f;
+      if (!in_pair && own.x == 0.f && own.y == 0.f && own.z == 0.f && own.w == 0.f && Sm0 == 0.f &&
+          Sp0 == 0.f)
+        continue;
+      const int e = atomicAdd(&s_nlist, 1);
+      if (e < bw_cap)
+        s_list[e] = (uint32_t)k;
+      else
+        bw1_item(k);
+    }
+    __syncthreads();
+    // (1b) the listed items, any thread
+    {
+      const int n_list = min(s_nlist, bw_cap);
+      for (int e = tid; e < n_list; e += nthr) bw1_item((int)s_list[e]);
     }
     __syncthreads();
     // (2) per (state, joint): sum over the spheres on links at or after the
