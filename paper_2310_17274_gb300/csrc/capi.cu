@@ -151,6 +151,18 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
     groups.back().w += 1;
   }
   const int G = (int)groups.size();
+  // spheres by link (ascending index within a link)
+  std::vector<int> lstart(D + 1, 0), lsph(M > 0 ? M : 1);
+  int max_ls = 0;
+  for (int i = 0; i < M; ++i) lstart[d->sphere_link[i] + 1] += 1;
+  for (int l = 0; l < D; ++l) {
+    max_ls = std::max(max_ls, lstart[l + 1]);
+    lstart[l + 1] += lstart[l];
+  }
+  {
+    std::vector<int> fill(lstart.begin(), lstart.end() - 1);
+    for (int i = 0; i < M; ++i) lsph[fill[d->sphere_link[i]]++] = i;
+  }
   // one blob: fixed_tf | lim | spheres (float4) | axis | link | offsets | link spheres | pairs |
   // original positions | groups
   const size_t n_fix = (size_t)(D + 1) * 12, n_lim = (size_t)5 * D;
@@ -160,7 +172,8 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
                o_axis = take((size_t)D * 4), o_link = take((size_t)M * 4),
                o_soff = take((size_t)M * 4), o_lbs = take((size_t)D * 16), o_ldm = take((size_t)D * 4),
                o_pairs = take((size_t)(P > 0 ? P : 1) * 4), o_orig = take((size_t)(P > 0 ? P : 1) * 4),
-               o_grp = take((size_t)(G > 0 ? G : 1) * 16);
+               o_grp = take((size_t)(G > 0 ? G : 1) * 16), o_lst = take((size_t)(D + 1) * 4),
+               o_lsp = take((size_t)(M > 0 ? M : 1) * 4);
   std::vector<unsigned char> host(off, 0);
   std::memcpy(host.data() + o_fix, d->fixed_tf, n_fix * 4);
   float* lim = reinterpret_cast<float*>(host.data() + o_lim);
@@ -182,6 +195,8 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
     std::memcpy(host.data() + o_orig, orig.data(), (size_t)P * 4);
   }
   if (G > 0) std::memcpy(host.data() + o_grp, groups.data(), (size_t)G * 16);
+  std::memcpy(host.data() + o_lst, lstart.data(), (size_t)(D + 1) * 4);
+  std::memcpy(host.data() + o_lsp, lsph.data(), (size_t)M * 4);
   void* dev = nullptr;
   cudaError_t e = cudaMalloc(&dev, off);
   if (e != cudaSuccess) return fail(CR_ENOMEM, "cudaMalloc(%zu): %s", off, cudaGetErrorString(e));
@@ -211,6 +226,9 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
   r->view.sphere_off = reinterpret_cast<const float*>(b + o_soff);
   r->view.link_bs = reinterpret_cast<const float4*>(b + o_lbs);
   r->view.link_dmax = reinterpret_cast<const float*>(b + o_ldm);
+  r->view.link_start = reinterpret_cast<const int*>(b + o_lst);
+  r->view.link_sph = reinterpret_cast<const int*>(b + o_lsp);
+  r->view.max_link_spheres = max_ls;
   for (int j = 0; j < D; ++j) {
     r->q_lo[j] = d->q_lo[j];
     r->q_hi[j] = d->q_hi[j];

@@ -58,6 +58,9 @@ struct RobotView {
   const uint32_t* pairs;    // [P] i | (j << 16), grouped by link pair
   const int* pair_orig;     // [P] position of each pair in the caller's list (ties: first wins)
   const int4* groups;       // [G] (link a, link b, first pair, pair count)
+  const int* link_start;    // [dof+1] spheres of link l are link_sph[link_start[l] .. link_start[l+1])
+  const int* link_sph;      // [M] sphere indices ordered by link
+  int max_link_spheres;     // largest sphere count of a link
 };
 
 // One box packed as five float4 rows: (R^T row k, t_k) for k = 0..2 so that
@@ -109,7 +112,7 @@ struct EvalArgs {
 // tile are kept (read by all later passes); without, they are recomputed
 // from the link transforms (long horizons that would not fit).
 struct EvalSmem {
-  int off_fix, off_lim, off_sph, off_link, off_soff, off_lbs, off_ldm, off_pairs, off_grp, off_th,
+  int off_fix, off_lim, off_sph, off_link, off_soff, off_lbs, off_ldm, off_lst, off_lsp, off_pairs, off_grp, off_th,
       off_lt, off_sc, off_x, off_sg, off_nz, off_rho, off_lm, off_mask, off_gmask, off_stw,
       off_sts, off_sta, off_gth, off_wsph, off_box, off_ee, off_sten, off_pb, off_db, off_sm, off_goal,
       off_free, bytes;
@@ -125,6 +128,8 @@ struct EvalSmem {
     off_soff = take(M * 4);
     off_lbs = take(dof * 16);
     off_ldm = take(dof * 4);
+    off_lst = take((dof + 1) * 4);
+    off_lsp = take(M * 4);
     off_pairs = take(P * 4);
     off_grp = take(G * 16);
     off_th = take(max_states * dof * 4);

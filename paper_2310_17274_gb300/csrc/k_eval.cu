@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   __shared__ int s_axis[kMaxDof];
   __shared__ int s_next;
   __shared__ int s_nlist;
+  __shared__ int s_nll;
 
   const int D = a.rb.dof, M = a.rb.n_spheres, P = a.rb.n_pairs, G = a.rb.n_groups;
   const int GW = (G + 31) / 32;
@@ -219,6 +220,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   float* s_soff = reinterpret_cast<float*>(smem + L.off_soff);
   float4* s_lbs = reinterpret_cast<float4*>(smem + L.off_lbs);
   float* s_ldm = reinterpret_cast<float*>(smem + L.off_ldm);
+  int* s_lst = reinterpret_cast<int*>(smem + L.off_lst);
+  int* s_lsp = reinterpret_cast<int*>(smem + L.off_lsp);
   uint32_t* s_pairs = reinterpret_cast<uint32_t*>(smem + L.off_pairs);
   int4* s_grp = reinterpret_cast<int4*>(smem + L.off_grp);
   float* s_th = reinterpret_cast<float*>(smem + L.off_th);
@@ -249,6 +252,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   uint32_t* s_list = reinterpret_cast<uint32_t*>(smem + L.off_sten);
   const int list_cap = (L.off_pb - L.off_sten) / 12;
   const int bw_cap = (L.off_pb - L.off_sten) / 4;  // the backward pass's list, same region
+  // the (state, link) items with boxes in reach: S * D entries in the bound outputs
+  int* s_llist = reinterpret_cast<int*>(smem + L.off_pb);
 
   // robot model, once per CTA
   for (int k = tid; k < (D + 1) * 12; k += nthr) s_fix[k] = a.rb.fixed_tf[k];
@@ -262,6 +267,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     s_lbs[k] = a.rb.link_bs[k];
     s_ldm[k] = a.rb.link_dmax[k];
   }
+  for (int k = tid; k <= D; k += nthr) s_lst[k] = a.rb.link_start[k];
+  for (int k = tid; k < M; k += nthr) s_lsp[k] = a.rb.link_sph[k];
   for (int k = tid; k < P; k += nthr) s_pairs[k] = a.rb.pairs[k];
   for (int k = tid; k < G; k += nthr) s_grp[k] = a.rb.groups[k];
   for (int k = tid; k < D; k += nthr) s_axis[k] = a.rb.axis[k];
@@ -472,7 +479,10 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
           float4* dst = reinterpret_cast<float4*>(s_box);
           constexpr int kRow = (int)(sizeof(BoxRows) / 16);
           for (int k = tid; k < kc * kRow; k += nthr) dst[k] = src[k];
-          if (tid == 0) s_nlist = 0;
+          if (tid == 0) {
+            s_nlist = 0;
+            s_nll = 0;
+          }
         }
         __syncthreads();
         // (1) per (state, link): bitmask of the boxes within reach
@@ -499,6 +509,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
           }
           s_mask[2 * k] = (uint32_t)m;
           s_mask[2 * k + 1] = (uint32_t)(m >> 32);
+          if (m) s_llist[atomicAdd(&s_nll, 1)] = k;  // at most S * D entries: always fits
         }
         __syncthreads();
         // (2) the sweep of a (state, sphere) over the boxes in mask m, in box order
@@ -555,16 +566,20 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
           s_sg[k] = acc4;
           if (!clear) s_free[r] = 0;
         };
-        // (2a) per (state, sphere): the boxes of its link's mask that are within
-        //      the link-level bound of the sphere; the few items with any go to a
-        //      list (inline when the list is full) so that (2b) runs them densely
-        for (int k = tid; k < S * M; k += nthr) {
-          const int sg = k / M, i = k % M;
+        // (2a) per sphere of a listed (state, link): the boxes of the link's mask
+        //      within the link-level bound of the sphere; the few items with any
+        //      go to a list (inline when the list is full) so that (2b) runs
+        //      them densely
+        const int n_ll = s_nll, spl = a.rb.max_link_spheres;
+        for (int w = tid; w < n_ll * spl; w += nthr) {
+          const int sl0 = s_llist[w / spl], jl = w % spl;
+          const int sg = sl0 / D, l = sl0 % D;
+          if (jl >= s_lst[l + 1] - s_lst[l]) continue;
+          const int i = s_lsp[s_lst[l] + jl];
+          const int k = sg * M + i;
           const float rad = s_sph[i].w;
           if (rad < 0.f) continue;
-          const int sl0 = sg * D + s_link[i];
           unsigned long long m0 = (unsigned long long)s_mask[2 * sl0] | ((unsigned long long)s_mask[2 * sl0 + 1] << 32);
-          if (!m0) continue;
           const int r = sg / H;
           // boxes within the link-level bound of this sphere's reach first
           unsigned long long m = 0ull;
