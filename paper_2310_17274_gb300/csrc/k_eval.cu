@@ -40,10 +40,13 @@ __device__ __forceinline__ V3 cross(V3 a, V3 b) {
 __device__ __forceinline__ float norm(V3 a) { return sqrtf(dot(a, a)); }
 
 // point x (link frame centre c) through a row-major 3x4 [R|p]
+// T: 16-byte aligned 3x4 transform (three float4 rows)
 __device__ __forceinline__ V3 tf_point(const float* T, float cx, float cy, float cz) {
-  return v3(fmaf(T[0], cx, fmaf(T[1], cy, fmaf(T[2], cz, T[3]))),
-            fmaf(T[4], cx, fmaf(T[5], cy, fmaf(T[6], cz, T[7]))),
-            fmaf(T[8], cx, fmaf(T[9], cy, fmaf(T[10], cz, T[11]))));
+  const float4* R = reinterpret_cast<const float4*>(T);
+  const float4 a = R[0], b = R[1], c = R[2];
+  return v3(fmaf(a.x, cx, fmaf(a.y, cy, fmaf(a.z, cz, a.w))),
+            fmaf(b.x, cx, fmaf(b.y, cy, fmaf(b.z, cz, b.w))),
+            fmaf(c.x, cx, fmaf(c.y, cy, fmaf(c.z, cz, c.w))));
 }
 
 // Serial chain (Sec. 3.1): T_j = T_{j-1} F_j J_axis(theta_j), where F_j J is
@@ -962,7 +965,7 @@ __global__ void k_fk(RobotView rb, const float* __restrict__ theta, int n, float
   if (b >= n) return;
   float q[kMaxDof];
   for (int j = 0; j < D; ++j) q[j] = theta[(long long)b * D + j];
-  float LT[kMaxDof * 12];
+  alignas(16) float LT[kMaxDof * 12];
   fk_chain(s_fix, s_axis, D, q, nullptr, LT);
   if (link_tf)
     for (int k = 0; k < D * 12; ++k) link_tf[(long long)b * D * 12 + k] = LT[k];
