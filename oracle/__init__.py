@@ -109,6 +109,9 @@ def lib():
         L.cro_lbfgs_direction.argtypes = [C.POINTER(_Lbfgs), _dp]
         L.cro_ls_candidates.argtypes = [C.POINTER(_Params), C.c_int32, C.c_int32, _dp, _dp,
                                         _dp, _dp, _dp]
+        L.cro_particle_sample.argtypes = [C.c_int32, C.c_int32, _dp, _dp, _dp, _dp]
+        L.cro_particle_update.argtypes = [C.c_int32, C.c_int32, _dp, _dp, C.c_double, C.c_double,
+                                          C.c_double, _dp, _dp, _dp]
         L.cro_ls_select.argtypes = [C.POINTER(_Params), C.c_int32, C.c_double, _dp, _dp, _dp,
                                     _dp, _dp]
         L.cro_ls_select.restype = C.c_int32
@@ -406,3 +409,28 @@ def start_collides_with_box(rb, q_start, pose7, half_ext):
         if phi - sp[i, 3] <= 0:
             return True
     return False
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4.2 particle-based optimisation
+# ---------------------------------------------------------------------------
+
+def particle_sample(mu, sigma, eps):
+    """particles [n_p, n] = mu + sqrt(sigma) * eps (eps [n_p, n])."""
+    mu, sigma, eps = _f64(mu), _f64(sigma), _f64(eps)
+    n = mu.size
+    n_p = eps.size // n
+    out = np.zeros((n_p, n))
+    lib().cro_particle_sample(n, n_p, _p(mu), _p(sigma), _p(eps), _p(out))
+    return out
+
+
+def particle_update(cost, particles, mu, sigma, beta, k_mu, k_sigma):
+    """One UPDATE of the particle optimiser; returns (mu, sigma, weights)."""
+    cost, particles = _f64(cost), _f64(particles)
+    mu, sigma = _f64(mu).copy(), _f64(sigma).copy()
+    n, n_p = mu.size, cost.size
+    w = np.zeros(n_p)
+    lib().cro_particle_update(n, n_p, _p(cost), _p(particles), float(beta), float(k_mu),
+                              float(k_sigma), _p(mu), _p(sigma), _p(w))
+    return mu, sigma, w

@@ -828,3 +828,43 @@ void cro_solve(const cro_robot* rb, const cro_world* w, const double* q_start,
   free(x); free(g); free(c); free(cf); free(xp); free(gp); free(S); free(Y); free(rho); free(it);
   free(d); free(cand); free(cc); free(cg); free(ccf);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4.2 particle-based optimisation                                       */
+/* ------------------------------------------------------------------------ */
+
+void cro_particle_sample(int32_t n, int32_t n_p, const double* mu, const double* sigma,
+                         const double* eps, double* particles) {
+  for (int32_t i = 0; i < n_p; ++i)
+    for (int32_t k = 0; k < n; ++k)
+      particles[(size_t)i * n + k] = mu[k] + sqrt(sigma[k]) * eps[(size_t)i * n + k];
+}
+
+void cro_particle_update(int32_t n, int32_t n_p, const double* cost, const double* particles,
+                         double beta, double k_mu, double k_sigma, double* mu, double* sigma,
+                         double* w) {
+  /* exponential utility of c = -cost / beta */
+  double cmin = cost[0];
+  for (int32_t i = 1; i < n_p; ++i)
+    if (cost[i] < cmin) cmin = cost[i];
+  double* wt = (double*)malloc((size_t)n_p * sizeof(double));
+  double z = 0.0;
+  for (int32_t i = 0; i < n_p; ++i) {
+    wt[i] = exp(-(cost[i] - cmin) / beta);
+    z += wt[i];
+  }
+  for (int32_t i = 0; i < n_p; ++i) wt[i] /= z;
+  /* Eq. 12 and Eq. 13, both from the previous mean */
+  for (int32_t k = 0; k < n; ++k) {
+    double m = 0.0, v = 0.0;
+    for (int32_t i = 0; i < n_p; ++i) {
+      double th = particles[(size_t)i * n + k];
+      m += wt[i] * th;
+      v += wt[i] * (th - mu[k]) * (th - mu[k]);
+    }
+    sigma[k] = (1.0 - k_sigma) * sigma[k] + k_sigma * v;
+    mu[k] = (1.0 - k_mu) * mu[k] + k_mu * m;
+  }
+  if (w) memcpy(w, wt, (size_t)n_p * sizeof(double));
+  free(wt);
+}

@@ -176,6 +176,26 @@ void cro_solve(const cro_robot* rb, const cro_world* w, const double* q_start,
                const double* seeds, int32_t iters, double* best_x, double* best_c,
                uint8_t* best_cfree);
 
+/* ------------------------------------------------------------------------ */
+/* Sec. 4.2 particle-based optimisation (Eq. 12, Eq. 13, Alg. "Particle-Based */
+/* Optimization"), one seed: mean mu [n] and diagonal covariance sigma [n].  */
+/* ------------------------------------------------------------------------ */
+
+/* SAMPLE: particles [n_p][n] = mu + sqrt(sigma) * eps, eps [n_p][n] the
+ * zero-mean unit Gaussian samples (drawn by the caller). */
+void cro_particle_sample(int32_t n, int32_t n_p, const double* mu, const double* sigma,
+                         const double* eps, double* particles);
+
+/* UPDATE: exponential utility w_i = e^{c_i} / sum_j e^{c_j}, c = -cost / beta
+ * (evaluated after subtracting the smallest cost, which leaves w unchanged);
+ * mu <- (1 - k_mu) mu + k_mu sum_i w_i theta_i (Eq. 12);
+ * sigma <- (1 - k_sigma) sigma + k_sigma sum_i w_i (theta_i - mu_prev)^2
+ * (Eq. 13 as read: the printed update is garbled).  Writes w [n_p] if not
+ * NULL; mu and sigma are updated in place. */
+void cro_particle_update(int32_t n, int32_t n_p, const double* cost, const double* particles,
+                         double beta, double k_mu, double k_sigma, double* mu, double* sigma,
+                         double* w);
+
 #ifdef __cplusplus
 }
 #endif

@@ -722,3 +722,77 @@ def test_solve_best_cost_never_increases(oracle_mod):
         ev = oracle_mod.evaluate(rb, w, qs, pr.goal, out["x"])
         np.testing.assert_allclose(ev["cost"], out["cost"], rtol=1e-12)
     assert np.all(prev < init)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4.2 particle-based optimisation (Eq. 12, Eq. 13)
+# ---------------------------------------------------------------------------
+
+def test_particle_sample_closed_forms(oracle_mod):
+    mu = np.array([0.5, -1.0, 2.0])
+    sigma = np.array([4.0, 0.25, 0.0])
+    eps = np.array([[0.0, 0.0, 0.0], [1.0, -2.0, 3.0]])
+    p = oracle_mod.particle_sample(mu, sigma, eps)
+    assert np.array_equal(p[0], mu)                       # zero noise: the mean
+    assert np.allclose(p[1], [0.5 + 2.0, -1.0 - 1.0, 2.0])  # sqrt(sigma) scales the noise
+
+
+def test_particle_equal_costs_reduce_to_plain_averages(oracle_mod):
+    rng = np.random.default_rng(0)
+    n, n_p = 5, 7
+    th = rng.normal(size=(n_p, n))
+    mu, sigma = rng.normal(size=n), rng.uniform(0.1, 1.0, size=n)
+    k_mu, k_s = 0.3, 0.6
+    m2, s2, w = oracle_mod.particle_update(np.full(n_p, 3.25), th, mu, sigma, 0.7, k_mu, k_s)
+    assert np.allclose(w, 1.0 / n_p)
+    assert np.allclose(m2, (1 - k_mu) * mu + k_mu * th.mean(axis=0), atol=1e-14)
+    assert np.allclose(s2, (1 - k_s) * sigma + k_s * ((th - mu) ** 2).mean(axis=0), atol=1e-14)
+
+
+def test_particle_weights_follow_exponential_utility(oracle_mod):
+    th = np.array([[0.0], [1.0]])
+    beta = 2.5
+    _, _, w = oracle_mod.particle_update(np.array([10.0, 13.0]), th, [0.0], [1.0], beta, 1.0, 1.0)
+    assert np.isclose(w.sum(), 1.0) and np.all(w > 0)
+    assert np.isclose(w[1] / w[0], np.exp(-(13.0 - 10.0) / beta))   # c = -C / beta
+    # a common shift of every cost changes nothing
+    _, _, w2 = oracle_mod.particle_update(np.array([1e6 + 10.0, 1e6 + 13.0]), th, [0.0], [1.0], beta,
+                                          1.0, 1.0)
+    assert np.allclose(w2, w, rtol=1e-12)
+
+
+def test_particle_temperature_limits(oracle_mod):
+    rng = np.random.default_rng(1)
+    n, n_p = 4, 6
+    th = rng.normal(size=(n_p, n))
+    cost = rng.uniform(0.0, 10.0, size=n_p)
+    mu, sigma = np.zeros(n), np.ones(n)
+    best = int(np.argmin(cost))
+    # beta -> 0: all weight on the cheapest particle
+    m2, s2, w = oracle_mod.particle_update(cost, th, mu, sigma, 1e-9, 1.0, 1.0)
+    assert np.isclose(w[best], 1.0) and np.allclose(m2, th[best]) and np.allclose(s2, th[best] ** 2)
+    # beta -> infinity: uniform weights
+    _, _, w = oracle_mod.particle_update(cost, th, mu, sigma, 1e12, 1.0, 1.0)
+    assert np.allclose(w, 1.0 / n_p)
+
+
+def test_particle_rates_zero_keep_state_and_one_particle_replaces_it(oracle_mod):
+    mu, sigma = np.array([0.2, -0.4]), np.array([0.3, 0.5])
+    th = np.array([[1.0, 2.0]])
+    m2, s2, _ = oracle_mod.particle_update([7.0], th, mu, sigma, 1.0, 0.0, 0.0)
+    assert np.array_equal(m2, mu) and np.array_equal(s2, sigma)
+    m2, s2, _ = oracle_mod.particle_update([7.0], th, mu, sigma, 1.0, 1.0, 1.0)
+    assert np.allclose(m2, th[0]) and np.allclose(s2, (th[0] - mu) ** 2)   # deviation from the old mean
+
+
+def test_particle_covariance_recovers_sampling_variance(oracle_mod):
+    """Equal costs, k = 1: the new covariance is the weighted second moment of
+    the particles about the old mean, which for mu + sqrt(sigma) * N(0, 1)
+    samples converges to sigma."""
+    rng = np.random.default_rng(2)
+    mu, sigma = np.array([0.3, -0.7, 1.1]), np.array([0.04, 0.25, 1.0])
+    eps = rng.standard_normal((200000, 3))
+    th = oracle_mod.particle_sample(mu, sigma, eps)
+    m2, s2, _ = oracle_mod.particle_update(np.zeros(len(th)), th, mu, sigma, 1.0, 1.0, 1.0)
+    assert np.allclose(s2, sigma, rtol=0.02)
+    assert np.allclose(m2, mu, atol=0.01)
