@@ -60,6 +60,12 @@ def whole_job_rate(units_per_rank: float, steps: int, world_size: int, t_max: fl
 # workload (synthetic, seeded)
 # ---------------------------------------------------------------------------
 
+def start_config(synth, rb, seed_offset=0):
+    """q_start of the trajectory workload, drawn from its own stream (the
+    problem's stream, seed 2, draws q_goal)."""
+    return synth.uniform_config(np.random.default_rng(1002 + seed_offset), rb)
+
+
 def make_workload(crgb, synth, seed_offset=0):
     """Trajectory-optimisation problem; goal and box rejection through the
     library's own kinematics / evaluation (no oracle on this path)."""
@@ -67,8 +73,7 @@ def make_workload(crgb, synth, seed_offset=0):
     cfg = synth.CONFIGS["trajopt"]
     rb = synth.make_robot(cfg.spheres_per_link, seed=0)
     R = crgb.Robot(rb)
-    rng = np.random.default_rng(2 + seed_offset)
-    qs = synth.uniform_config(rng, rb)
+    qs = start_config(synth, rb, seed_offset)
 
     def goal_fn(q):
         _, ee, _ = crgb.fk(R, torch.tensor(q, dtype=torch.float32, device="cuda")[None], spheres=False)
@@ -204,8 +209,7 @@ def run_reference(args):
     oracle.build()
     cfg = synth.CONFIGS["trajopt"]
     rb = synth.make_robot(cfg.spheres_per_link, seed=0)
-    rng = np.random.default_rng(2)
-    qs = synth.uniform_config(rng, rb)
+    qs = start_config(synth, rb)
     world = synth.make_world(cfg.n_boxes, cfg.world_seed,
                              lambda p, h: oracle.start_collides_with_box(rb, qs, p, h))
     pr = synth.make_problem(rb, world, 2, cfg.n_seeds, cfg.horizon,
@@ -239,8 +243,7 @@ def cpu_baseline(seconds=10.0):
     oracle.build()
     cfg = synth.CONFIGS["trajopt"]
     rb = synth.make_robot(cfg.spheres_per_link, seed=0)
-    rng = np.random.default_rng(2)
-    qs = synth.uniform_config(rng, rb)
+    qs = start_config(synth, rb)
     world = synth.make_world(cfg.n_boxes, cfg.world_seed,
                              lambda p, h: oracle.start_collides_with_box(rb, qs, p, h))
     pr = synth.make_problem(rb, world, 2, cfg.n_seeds, cfg.horizon,
@@ -268,7 +271,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="crgb")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="ik,uneven,plain,serve")
+    ap.add_argument("--extras", default="ik,uneven,plain,serve,particle")
     ap.add_argument("--serve-rates", default="500,100")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--profile", type=int, default=0,
@@ -428,6 +431,8 @@ def main():
     if rank == 0 and "ik" in want:
         extras["ik"] = bench_ik(crgb, synth, ctx, R, rb)
         extras["ik_no_collision"] = bench_ik(crgb, synth, ctx, R, rb, collision=False)
+    if rank == 0 and "particle" in want:
+        extras["particle"] = bench_particle(crgb, synth, ctx, R, rb, world, pr, P, iters)
     if rank == 0 and "uneven" in want:
         extras["uneven"] = bench_uneven(crgb, synth, ctx, R, rb)
     if rank == 0 and "serve" in want:
@@ -548,6 +553,52 @@ def _quat_rot(q):
     return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
                      [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def bench_particle(crgb, synth, ctx, R, rb, world, pr, P, iters, n_particles=16, n_iters=2,
+                   beta=100.0, k_mu=0.9, k_sigma=0.9, sigma0=0.01):
+    """Sec. 4.2: n_iters particle iterations (n_particles per seed, unit
+    Gaussian samples drawn on the device from a fixed generator seed) before
+    the L-BFGS solve of the trajectory workload, against the same solve from
+    the raw seeds: time and final best costs."""
+    import torch
+    B, H, D = pr.seeds.shape
+    W = crgb.World(world)
+    spec = crgb.ProblemSpec(W, pr.q_start, pr.goal, H)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(123)
+    eps = torch.randn((n_iters, B, n_particles, H, D), device="cuda", generator=gen)
+    seeds0 = torch.tensor(pr.seeds, dtype=torch.float32, device="cuda")
+    sspec = crgb.ProblemSpec(W, pr.q_start, pr.goal, H, seeds=pr.seeds)
+
+    def run(particles):
+        mu = seeds0.clone()
+        if particles:
+            sg = torch.full_like(mu, sigma0)
+            for k in range(n_iters):
+                crgb.particle_step(R, spec, mu, sg, eps[k], params=P, beta=beta, k_mu=k_mu,
+                                   k_sigma=k_sigma)
+        return crgb.solve(ctx, R, [sspec], P, iters=iters, graph=True, persistent=True,
+                          device_seeds=[mu])[0]
+
+    out = {}
+    for particles in (False, True):
+        for _ in range(2):
+            run(particles)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        o = run(particles)
+        e1.record()
+        torch.cuda.synchronize()
+        c = o.cost.cpu().numpy()
+        f = o.cfree.cpu().numpy().astype(bool)
+        out["particle+lbfgs" if particles else "lbfgs"] = {
+            "ms": e0.elapsed_time(e1), "best_cost": float(c[int(o.best)]),
+            "median_seed_cost": float(np.median(c)), "collision_free_seeds": int(f.sum())}
+    out.update({"particles_per_seed": n_particles, "particle_iters": n_iters, "beta": beta,
+                "k_mu": k_mu, "k_sigma": k_sigma, "sigma0": sigma0})
+    return out
 
 
 def bench_uneven(crgb, synth, ctx, R, rb, iters=100):

@@ -214,6 +214,32 @@ cr_status cr_opt_propose(const cr_robot* robot, const cr_params* params, const c
 cr_status cr_opt_select(const cr_robot* robot, const cr_params* params, const cr_opt_state* st,
                         void* stream);
 
+/* Particle-based optimisation (Sec. 4.2, Eq. 12-13, Alg. "Particle-Based
+ * Optimization"): one iteration for n_seeds seeds of one problem, run before
+ * L-BFGS to move seeds into a better basin.
+ *   SAMPLE  particles = mu + sqrt(sigma) * eps (no clipping to the limits;
+ *           the bound cost of Eq. 17 penalises what leaves them)
+ *   COST    cr_eval of every particle (cost only)
+ *   UPDATE  w_i = e^{c_i} / sum_j e^{c_j} with c = -cost / beta (computed
+ *           after subtracting the smallest cost, which leaves w unchanged);
+ *           mu <- (1 - k_mu) mu + k_mu sum_i w_i theta_i (Eq. 12);
+ *           sigma <- (1 - k_sigma) sigma + k_sigma sum_i w_i (theta_i - mu)^2
+ *           with the previous mu (Eq. 13 is garbled as printed; this reading
+ *           makes sigma the weighted second moment of the particles)
+ *   mu, sigma   device [n_seeds][H][dof] mean and diagonal covariance,
+ *               updated in place (sigma >= 0)
+ *   eps         device [n_seeds][n_particles][H][dof] zero-mean unit Gaussian
+ *               samples drawn by the caller (the library draws no random numbers)
+ *   particles   device [n_seeds][n_particles][H][dof] scratch; holds the
+ *               samples on return
+ *   cost        device [n_seeds][n_particles] scratch; their costs on return
+ *   beta > 0, k_mu and k_sigma in [0, 1]: the paper gives no values.
+ * Three launches on `stream`; deterministic (fixed summation orders). */
+cr_status cr_particle_step(const cr_robot* robot, const cr_problem* problem, const cr_params* params,
+                           int32_t n_seeds, int32_t n_particles, float* mu, float* sigma,
+                           const float* eps, float* particles, float* cost, float beta, float k_mu,
+                           float k_sigma, void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Runtime: context, batched solve                                            */
 /* ------------------------------------------------------------------------- */

@@ -91,6 +91,8 @@ SIGNATURES = {
     "cr_context_destroy": ([_vp], None),
     "cr_solve": ([_vp, _vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), C.c_int32, C.c_uint32,
                   C.POINTER(Result), _vp], C.c_int32),
+    "cr_particle_step": ([_vp, C.POINTER(Problem), C.POINTER(Params), C.c_int32, C.c_int32, _vp,
+                          _vp, _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, _vp], C.c_int32),
     "cr_autotune": ([_vp, _vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), C.c_int32,
                      C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                      C.POINTER(C.c_float)], C.c_int32),
@@ -290,6 +292,29 @@ def evaluate(robot: Robot, problem: ProblemSpec, theta, params=None, want_grad=T
     check(lib().cr_eval(robot.handle, C.byref(pr), C.byref(P), _dptr(theta), B, _dptr(cost),
                         _dptr(grad), _dptr(cfree), _dptr(terms), _stream(stream)), "cr_eval")
     return dict(cost=cost, grad=grad, cfree=cfree, terms=terms)
+
+
+def particle_step(robot: Robot, problem: ProblemSpec, mu, sigma, eps, params=None, beta=1.0,
+                  k_mu=0.9, k_sigma=0.9, particles=None, cost=None, stream=None):
+    """One particle-optimisation iteration (cr_particle_step) for the seeds of
+    one problem.  mu, sigma: CUDA float32 [B, H, dof], updated in place; eps:
+    [B, n_particles, H, dof] unit Gaussian samples.  Returns (particles, cost)."""
+    import torch
+    B, n_p = eps.shape[0], eps.shape[1]
+    if particles is None:
+        particles = torch.empty_like(eps)
+    if cost is None:
+        cost = torch.empty((B, n_p), device=eps.device)
+    P = params if isinstance(params, Params) else make_params(params)
+    pr = problem.struct()
+    for t in (mu, sigma, eps, particles, cost):
+        if not t.is_contiguous():
+            raise ValueError("particle_step: tensors must be contiguous")
+    check(lib().cr_particle_step(robot.handle, C.byref(pr), C.byref(P), int(B), int(n_p), _dptr(mu),
+                                 _dptr(sigma), _dptr(eps), _dptr(particles), _dptr(cost),
+                                 float(beta), float(k_mu), float(k_sigma), _stream(stream)),
+          "cr_particle_step")
+    return particles, cost
 
 
 class OptBuffers:
