@@ -322,10 +322,15 @@ cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* p
     a.grad = cand ? st.cand_grad : st.g;
     a.cfree = cand ? st.cand_cfree : st.best_cfree;
     a.terms = nullptr;
-    a.queue = persistent ? queue : nullptr;
+    a.queue = nullptr;
     a.no_store_x = pl.no_store_x;
     return a;
   };
+  // Persistent form: a grid of resident CTAs taking tiles from a device
+  // counter, used when there are more tiles than resident CTAs (the counter
+  // then balances uneven tiles); with fewer, one CTA per tile is cheaper.
+  // The counter is zeroed before the first evaluation and by every optimiser
+  // launch after the evaluation it follows.
   auto launch_eval_batch = [&](bool cand) -> cr_status {
     EvalArgs a = eval_args(cand);
     const int block = pl.block;
@@ -334,10 +339,10 @@ cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* p
     int grid = a.n_tiles;
     if (persistent) {
       const int per_sm = std::max(1, eval_blocks_per_sm(a, block));
-      grid = std::min(a.n_tiles, per_sm * ctx->n_sm);
-      // the first evaluation starts its counter here; later ones find it
-      // zeroed by the optimiser launch that precedes them
-      if (!cand) RT_CUDA(cudaMemsetAsync(queue, 0, sizeof(int), s));
+      if (a.n_tiles > per_sm * ctx->n_sm) {
+        grid = per_sm * ctx->n_sm;
+        a.queue = queue;
+      }
     }
     RT_CUDA(launch_eval(a, grid, block, s));
     return CR_OK;
@@ -358,6 +363,7 @@ cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* p
   RT_CUDA(cudaMemsetAsync(st.y, 0, (size_t)pl.V * pl.m * 4, s));
   RT_CUDA(cudaMemsetAsync(st.rho, 0, (size_t)pl.S * pl.m * 4, s));
   RT_CUDA(cudaMemsetAsync(st.iter, 0, (size_t)pl.S * 4, s));
+  if (persistent) RT_CUDA(cudaMemsetAsync(queue, 0, sizeof(int), s));
   cr_status rs = launch_eval_batch(false);
   if (rs != CR_OK) return rs;
   o.init_best = 1;

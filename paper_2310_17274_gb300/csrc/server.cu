@@ -299,12 +299,16 @@ cr_status launch_eval_set(cr_server* sv, Pool& pl, const ProblemView* probs, con
   a.grad = cand ? st.cand_grad : st.g;
   a.cfree = cand ? st.cand_cfree : st.best_cfree;
   a.no_store_x = -1;
-  a.queue = (int*)pl.p(pl.o_queue);
   const int block = kEvalBlock;
   if (eval_smem_bytes(a, block) > eval_smem_limit()) return failf(CR_EINVAL, "server: tile too large");
   const int per_sm = std::max(1, eval_blocks_per_sm(a, block));
-  SV_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int), pl.stream));
-  SV_CUDA(launch_eval(a, std::min(n_tiles, per_sm * sv->n_sm), block, pl.stream));
+  int grid = n_tiles;
+  if (n_tiles > per_sm * sv->n_sm) {  // more tiles than resident CTAs: take them from a counter
+    a.queue = (int*)pl.p(pl.o_queue);
+    grid = per_sm * sv->n_sm;
+    SV_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int), pl.stream));
+  }
+  SV_CUDA(launch_eval(a, grid, block, pl.stream));
   return CR_OK;
 }
 
