@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   __shared__ int s_next;
   __shared__ int s_nlist;
   __shared__ int s_nll;
+  __shared__ int s_nbw;
 
   const int D = a.rb.dof, M = a.rb.n_spheres, P = a.rb.n_pairs, G = a.rb.n_groups;
   const int GW = (G + 31) / 32;
@@ -323,6 +324,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     }
     for (int k = tid; k < S * M; k += nthr) s_sg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int k = tid; k < S * GW; k += nthr) s_gmask[k] = 0u;
+    if (tid == 0) s_nbw = 0;
     for (int k = tid; k < S * MW; k += nthr) s_nz[k] = 0u;
     __syncthreads();
     // joint sines and cosines of every slot, all threads at once
@@ -471,6 +473,22 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
       mo.thr = s_sph[i].w + fmaxf(eta, fmaxf(mo.L0, mo.L2));
       return mo;
     };
+
+    // Self-collision link pairs whose bounding spheres are within 1 mm (the
+    // pair search below skips the others); the world term's first barrier
+    // publishes the mask.
+    for (int k = tid; k < S * G; k += nthr) {
+      const int sg = k / G, g = k % G;
+      const int4 gr = s_grp[g];
+      const float4 A = s_rho[sg * D + gr.x], B = s_rho[sg * D + gr.y];
+      const float ra = s_lbs[gr.x].w, rb = s_lbs[gr.y].w;
+      if (ra >= 0.f && rb >= 0.f) {
+        const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
+        const float lim = ra + rb + 1e-3f;
+        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < lim * lim) atomicOr(&s_gmask[sg * GW + g / 32], 1u << (g % 32));
+      }
+    }
+    if (K == 0) __syncthreads();
 
     // ---- world term (Eq. 11 with the sweep of Sec. 3.4)
     if (K > 0) {
@@ -624,19 +642,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     }
 
     // ---- self-collision (Eq. 9): link pairs whose bounding spheres are more
-    // than 1 mm apart are skipped; the rest are searched pair by pair
-    for (int k = tid; k < S * G; k += nthr) {
-      const int sg = k / G, g = k % G;
-      const int4 gr = s_grp[g];
-      const float4 A = s_rho[sg * D + gr.x], B = s_rho[sg * D + gr.y];
-      const float ra = s_lbs[gr.x].w, rb = s_lbs[gr.y].w;
-      if (ra >= 0.f && rb >= 0.f) {
-        const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
-        const float lim = ra + rb + 1e-3f;
-        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < lim * lim) atomicOr(&s_gmask[sg * GW + g / 32], 1u << (g % 32));
-      }
-    }
-    __syncthreads();
+    // than 1 mm apart were skipped above; the rest are searched pair by pair,
+    // a warp per state
     for (int sg = warp; sg < S; sg += nw) {
       const int r = sg / H, t = sg % H + 1;
       const int sl = slot(r, t);
@@ -657,15 +664,16 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
           const int g = w * 32 + __ffs(gm) - 1;
           gm &= gm - 1u;
           const int4 gr = s_grp[g];
+#pragma unroll 4
           for (int p = gr.z + lane; p < gr.z + gr.w; p += 32) {
             const uint32_t pr = s_pairs[p];
             const float4 A = X[pr & 0xffffu], B = X[pr >> 16];
-            if (A.w <= 0.f || B.w <= 0.f) continue;
             const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
             const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float rs = A.w + B.w;
             const float lim = rs + 1e-3f;
-            if (d2 >= lim * lim) continue;  // separated by more than 1 mm: no effect
+            // disabled spheres, or separated by more than 1 mm: no effect
+            if (A.w <= 0.f || B.w <= 0.f || d2 >= lim * lim) continue;
             const float pen = rs - sqrtf(d2);
             if (!(-pen > 0.f)) touch = true;
             if (pen > best) {
@@ -770,8 +778,6 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     };
     // (1a) list the (state, sphere) items whose gradient can be non-zero:
     //      nothing reaches the others, their gradient and cost stay zero
-    if (tid == 0) s_nlist = 0;
-    __syncthreads();
     for (int k = tid; k < S * M; k += nthr) {
       const int sg = k / M, i = k % M;
       const int t = sg % H + 1;
@@ -787,7 +793,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
       if (!in_pair && own.x == 0.f && own.y == 0.f && own.z == 0.f && own.w == 0.f && Sm0 == 0.f &&
           Sp0 == 0.f)
         continue;
-      const int e = atomicAdd(&s_nlist, 1);
+      const int e = atomicAdd(&s_nbw, 1);
       if (e < bw_cap)
         s_list[e] = (uint32_t)k;
       else
@@ -796,7 +802,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     __syncthreads();
     // (1b) the listed items, any thread
     {
-      const int n_list = min(s_nlist, bw_cap);
+      const int n_list = min(s_nbw, bw_cap);
       for (int e = tid; e < n_list; e += nthr) bw1_item((int)s_list[e]);
     }
     __syncthreads();
