@@ -655,8 +655,10 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
         }
         __syncwarp();
       }
+      // deepest penetration and its pair; the caller's pair index (ties: the
+      // first pair in the caller's list) is fetched only for exact ties
       float best = 0.f;
-      int arg = -1, arg_orig = 0x7fffffff;
+      int arg = -1;
       bool touch = false;
       for (int w = 0; w < GW; ++w) {
         uint32_t gm = s_gmask[sg * GW + w];
@@ -679,13 +681,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
             if (pen > best) {
               best = pen;
               arg = p;
-              arg_orig = a.rb.pair_orig[p];
-            } else if (pen == best && pen > 0.f) {  // exact tie: first in the caller's list
-              const int o = a.rb.pair_orig[p];
-              if (o < arg_orig) {
-                arg = p;
-                arg_orig = o;
-              }
+            } else if (pen == best && pen > 0.f && a.rb.pair_orig[p] < a.rb.pair_orig[arg]) {
+              arg = p;  // exact tie: first in the caller's list
             }
           }
         }
@@ -694,11 +691,9 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
       for (int o = 16; o > 0; o >>= 1) {
         const float ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
-        const int oo = __shfl_xor_sync(0xffffffffu, arg_orig, o);
-        if (ob > best || (ob == best && ob > 0.f && oo < arg_orig)) {
+        if (ob > best || (ob == best && ob > 0.f && oa != arg && a.rb.pair_orig[oa] < a.rb.pair_orig[arg])) {
           best = ob;
           arg = oa;
-          arg_orig = oo;
         }
       }
       touch = __any_sync(0xffffffffu, touch);
