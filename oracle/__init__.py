@@ -31,7 +31,7 @@ _LIB_PATH = os.path.join(_HERE, "libcro.so")
 _lock = threading.Lock()
 _lib = None
 
-SWEPT, SPEED, SELF, WOLFE, STRONG_WOLFE, IK_MODE, VEL_COST = 1, 2, 4, 8, 16, 32, 64
+SWEPT, SPEED, SELF, WOLFE, STRONG_WOLFE, IK_MODE, VEL_COST, CSPACE_GOAL = 1, 2, 4, 8, 16, 32, 64, 128
 N_TERMS = 5
 MAX_ALPHA = 16
 
@@ -59,7 +59,8 @@ class _Params(C.Structure):
                 ("k_vel", C.c_double), ("eta", C.c_double), ("eta_bound", C.c_double),
                 ("dt", C.c_double), ("sweep_steps", C.c_int32), ("history", C.c_int32),
                 ("n_alpha", C.c_int32), ("alpha", C.c_double * MAX_ALPHA),
-                ("armijo_c1", C.c_double), ("wolfe_c2", C.c_double), ("flags", C.c_uint32)]
+                ("armijo_c1", C.c_double), ("wolfe_c2", C.c_double), ("flags", C.c_uint32),
+                ("w_cspace", C.c_double), ("k_cspace", C.c_double)]
 
 
 class _Lbfgs(C.Structure):
@@ -103,7 +104,7 @@ def lib():
         L.cro_stencil.argtypes = [C.c_int32, C.c_int32, _dp, _dp, C.c_double, _dp, _dp, _dp]
         L.cro_goal_cost.argtypes = [C.POINTER(_Params), _dp, _dp, _dp, _dp]
         L.cro_goal_cost.restype = C.c_double
-        L.cro_eval.argtypes = [C.POINTER(_Robot), C.POINTER(_World), _dp, _dp,
+        L.cro_eval.argtypes = [C.POINTER(_Robot), C.POINTER(_World), _dp, _dp, _dp,
                                C.POINTER(_Params), C.c_int32, _dp, C.c_int32, _dp, _dp, _up,
                                _dp, _dp]
         L.cro_lbfgs_direction.argtypes = [C.POINTER(_Lbfgs), _dp]
@@ -115,7 +116,7 @@ def lib():
         L.cro_ls_select.argtypes = [C.POINTER(_Params), C.c_int32, C.c_double, _dp, _dp, _dp,
                                     _dp, _dp]
         L.cro_ls_select.restype = C.c_int32
-        L.cro_solve.argtypes = [C.POINTER(_Robot), C.POINTER(_World), _dp, _dp,
+        L.cro_solve.argtypes = [C.POINTER(_Robot), C.POINTER(_World), _dp, _dp, _dp,
                                 C.POINTER(_Params), C.c_int32, C.c_int32, _dp, C.c_int32, _dp,
                                 _dp, _up]
         _lib = L
@@ -292,7 +293,7 @@ def goal_cost(params, ee, goal7):
 # whole evaluation and optimiser
 # ---------------------------------------------------------------------------
 
-def evaluate(rb, world, q_start, goal7, theta, params=None, want_grad=True):
+def evaluate(rb, world, q_start, goal7, theta, params=None, want_grad=True, goal_q=None):
     """Cost, gradient, collision-free flag, per-term costs and decision margin
     of trajectories theta [B,H,dof] (one problem)."""
     keep = _Keep()
@@ -306,7 +307,8 @@ def evaluate(rb, world, q_start, goal7, theta, params=None, want_grad=True):
     cfree = np.zeros(B, dtype=np.uint8)
     terms = np.zeros((B, N_TERMS))
     margin = np.zeros(B)
-    lib().cro_eval(C.byref(R), C.byref(W), _p(_f64(q_start)), _p(_f64(goal7)), C.byref(P),
+    gq = None if goal_q is None else _f64(goal_q)
+    lib().cro_eval(C.byref(R), C.byref(W), _p(_f64(q_start)), _p(_f64(goal7)), _p(gq), C.byref(P),
                    H, _p(th), B, _p(cost), _p(grad), _p(cfree, _up), _p(terms), _p(margin))
     return dict(cost=cost, grad=grad, cfree=cfree.astype(bool), terms=terms, margin=margin)
 
@@ -355,7 +357,7 @@ def ls_select(params, c0, g0, d, cand_cost, cand_grad):
     return idx, m.value
 
 
-def solve(rb, world, q_start, goal7, seeds, iters, params=None):
+def solve(rb, world, q_start, goal7, seeds, iters, params=None, goal_q=None):
     keep = _Keep()
     R = _robot(rb, keep)
     W = _world(world, keep)
@@ -365,7 +367,8 @@ def solve(rb, world, q_start, goal7, seeds, iters, params=None):
     bx = np.zeros_like(sd)
     bc = np.zeros(B)
     bf = np.zeros(B, dtype=np.uint8)
-    lib().cro_solve(C.byref(R), C.byref(W), _p(_f64(q_start)), _p(_f64(goal7)), C.byref(P), H,
+    gq = None if goal_q is None else _f64(goal_q)
+    lib().cro_solve(C.byref(R), C.byref(W), _p(_f64(q_start)), _p(_f64(goal7)), _p(gq), C.byref(P), H,
                     B, _p(sd), int(iters), _p(bx), _p(bc), _p(bf, _up))
     return dict(x=bx, cost=bc, cfree=bf.astype(bool))
 

@@ -96,6 +96,8 @@ void cro_params_default(cro_params* p) {
   p->armijo_c1 = 1e-4;      /* unstated (garbled in Alg. 1); textbook value */
   p->wolfe_c2 = 0.9;
   p->flags = CRO_SWEPT | CRO_SPEED | CRO_SELF | CRO_WOLFE;
+  p->w_cspace = 5000.0;     /* alpha_4, App. A.1 (Eq. 15) */
+  p->k_cspace = 50.0;       /* alpha_5 */
 }
 
 /* ------------------------------------------------------------------------ */
@@ -481,7 +483,8 @@ static void backward_state(const cro_robot* rb, const double* LT, const double* 
 }
 
 static void eval_one(const cro_robot* rb, const box_t* boxes, int32_t K, const double* q_start,
-                     const double* goal7, const cro_params* prm, int32_t H, const double* theta,
+                     const double* goal7, const double* goal_q, const cro_params* prm, int32_t H,
+                     const double* theta,
                      double* cost, double* grad, uint8_t* cfree, double* terms, double* margin) {
   const int D = rb->dof, M = rb->n_spheres;
   const int ik = (prm->flags & CRO_IK_MODE) != 0;
@@ -578,6 +581,17 @@ static void eval_one(const cro_robot* rb, const box_t* boxes, int32_t K, const d
                    GX + (size_t)t * M * 3, t == H ? ee : NULL, dp, dR, G + (size_t)(t - 1) * D);
   }
 
+  /* Eq. 15 joint-space goal term at the last state:
+   * alpha_4 logcosh(alpha_5 |theta_g - theta_H|^2) */
+  if ((prm->flags & CRO_CSPACE_GOAL) && goal_q) {
+    const double* thH = theta + (size_t)(H - 1) * D;
+    double r2 = 0.0;
+    for (int j = 0; j < D; ++j) r2 += (thH[j] - goal_q[j]) * (thH[j] - goal_q[j]);
+    term[4] += prm->w_cspace * logcosh(prm->k_cspace * r2);
+    double f = prm->w_cspace * prm->k_cspace * tanh(prm->k_cspace * r2);
+    for (int j = 0; j < D; ++j) G[(size_t)(H - 1) * D + j] += 2.0 * f * (thH[j] - goal_q[j]);
+  }
+
   /* Eq. 17 position bound on theta_1..theta_H */
   for (int t = 0; t < H; ++t) {
     for (int j = 0; j < D; ++j) {
@@ -649,7 +663,8 @@ static void eval_one(const cro_robot* rb, const box_t* boxes, int32_t K, const d
 }
 
 void cro_eval(const cro_robot* rb, const cro_world* w, const double* q_start, const double* goal7,
-              const cro_params* prm, int32_t H, const double* theta, int32_t B, double* cost,
+              const double* goal_q, const cro_params* prm, int32_t H, const double* theta, int32_t B,
+              double* cost,
               double* grad, uint8_t* cfree, double* terms, double* margin) {
   box_t* boxes = (box_t*)malloc((size_t)(w->n > 0 ? w->n : 1) * sizeof(box_t));
   for (int k = 0; k < w->n; ++k) {
@@ -658,7 +673,7 @@ void cro_eval(const cro_robot* rb, const cro_world* w, const double* q_start, co
   }
   size_t n = (size_t)H * rb->dof;
   for (int b = 0; b < B; ++b) {
-    eval_one(rb, boxes, w->n, q_start, goal7, prm, H, theta + b * n, cost + b,
+    eval_one(rb, boxes, w->n, q_start, goal7, goal_q, prm, H, theta + b * n, cost + b,
              grad ? grad + b * n : NULL, cfree ? cfree + b : NULL,
              terms ? terms + (size_t)b * CRO_N_TERMS : NULL, margin ? margin + b : NULL);
   }
@@ -775,7 +790,7 @@ int32_t cro_ls_select(const cro_params* prm, int32_t n, double c0, const double*
 /* ------------------------------------------------------------------------ */
 
 void cro_solve(const cro_robot* rb, const cro_world* w, const double* q_start,
-               const double* goal7, const cro_params* prm, int32_t H, int32_t B,
+               const double* goal7, const double* goal_q, const cro_params* prm, int32_t H, int32_t B,
                const double* seeds, int32_t iters, double* best_x, double* best_c,
                uint8_t* best_cfree) {
   const int32_t D = rb->dof, n = H * D, m = prm->history, na = prm->n_alpha;
@@ -796,7 +811,7 @@ void cro_solve(const cro_robot* rb, const cro_world* w, const double* q_start,
   uint8_t* ccf = (uint8_t*)malloc((size_t)B * na);
 
   memcpy(x, seeds, (size_t)B * n * sizeof(double));
-  cro_eval(rb, w, q_start, goal7, prm, H, x, B, c, g, cf, NULL, NULL);
+  cro_eval(rb, w, q_start, goal7, goal_q, prm, H, x, B, c, g, cf, NULL, NULL);
   memcpy(best_x, x, (size_t)B * n * sizeof(double));
   memcpy(best_c, c, (size_t)B * sizeof(double));
   memcpy(best_cfree, cf, (size_t)B);
@@ -810,7 +825,7 @@ void cro_solve(const cro_robot* rb, const cro_world* w, const double* q_start,
       cro_ls_candidates(prm, n, D, rb->q_lo, rb->q_hi, x + (size_t)b * n, d + (size_t)b * n,
                         cand + (size_t)b * na * n);
     }
-    cro_eval(rb, w, q_start, goal7, prm, H, cand, B * na, cc, cg, ccf, NULL, NULL);
+    cro_eval(rb, w, q_start, goal7, goal_q, prm, H, cand, B * na, cc, cg, ccf, NULL, NULL);
     for (int32_t b = 0; b < B; ++b) {
       int32_t l = cro_ls_select(prm, n, c[b], g + (size_t)b * n, d + (size_t)b * n,
                                 cc + (size_t)b * na, cg + (size_t)b * na * n, NULL);

@@ -33,6 +33,7 @@ extern "C" {
 #define CRO_STRONG_WOLFE 16u  /* strong variant of the Wolfe test */
 #define CRO_IK_MODE      32u  /* single-state problem: no stencil terms, no sweep, no speed */
 #define CRO_VEL_COST     64u  /* velocity logcosh of Eq. 16 over all samples (Q = all) */
+#define CRO_CSPACE_GOAL  128u /* Eq. 15 joint-space goal cost (needs goal_q) */
 
 /* Robot: serial revolute chain + sphere model (Sec. 3.1, App. E.1 kinematics data). */
 typedef struct {
@@ -74,6 +75,7 @@ typedef struct {
   double alpha[CRO_MAX_ALPHA];
   double armijo_c1, wolfe_c2;
   uint32_t flags;
+  double w_cspace, k_cspace;  /* alpha_4, alpha_5 (Eq. 15, with CRO_CSPACE_GOAL) */
 } cro_params;
 
 void cro_params_default(cro_params* p);
@@ -132,6 +134,7 @@ double cro_goal_cost(const cro_params* prm, const double* ee, const double* goal
  * terms [B][5] (may be NULL); margin [B] (may be NULL): smallest distance of
  * any discrete decision from its threshold, for tolerance bookkeeping. */
 void cro_eval(const cro_robot* rb, const cro_world* w, const double* q_start, const double* goal7,
+              const double* goal_q,
               const cro_params* prm, int32_t H, const double* theta, int32_t B, double* cost,
               double* grad, uint8_t* cfree, double* terms, double* margin);
 
@@ -172,7 +175,7 @@ int32_t cro_ls_select(const cro_params* prm, int32_t n, double c0, const double*
  * search and best-iterate tracking (Sec. 4.1).  seeds [B][H][dof].
  * best_x [B][H][dof], best_c [B], best_cfree [B]. */
 void cro_solve(const cro_robot* rb, const cro_world* w, const double* q_start,
-               const double* goal7, const cro_params* prm, int32_t H, int32_t B,
+               const double* goal7, const double* goal_q, const cro_params* prm, int32_t H, int32_t B,
                const double* seeds, int32_t iters, double* best_x, double* best_c,
                uint8_t* best_cfree);
 

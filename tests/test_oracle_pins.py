@@ -796,3 +796,59 @@ def test_particle_covariance_recovers_sampling_variance(oracle_mod):
     m2, s2, _ = oracle_mod.particle_update(np.zeros(len(th)), th, mu, sigma, 1.0, 1.0, 1.0)
     assert np.allclose(s2, sigma, rtol=0.02)
     assert np.allclose(m2, mu, atol=0.01)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 15 joint-space goal cost (App. A.1)
+# ---------------------------------------------------------------------------
+
+def test_cspace_goal_closed_form_and_zero_at_goal(oracle_mod):
+    """One trajectory whose last state differs from the goal configuration in
+    one joint by d: the goal term grows by alpha_4 logcosh(alpha_5 d^2); at the
+    goal it adds nothing, value or gradient."""
+    from paper_2310_17274_gb300 import synth
+    rb = synth.make_robot(synth.SPHERES_42, seed=0)
+    w = synth.World(pose=np.zeros((0, 7)), half_ext=np.zeros((0, 3)))
+    H = 4
+    rng = np.random.default_rng(3)
+    th = rng.uniform(-0.5, 0.5, size=(1, H, rb.dof))
+    q0 = th[0, 0].copy()
+    goal7 = np.array([0.3, 0.0, 0.4, 1.0, 0.0, 0.0, 0.0])
+    base = oracle_mod.evaluate(rb, w, q0, goal7, th)
+    p = dict(flags=oracle_mod.params_default()["flags"] | oracle_mod.CSPACE_GOAL)
+    at = oracle_mod.evaluate(rb, w, q0, goal7, th, p, goal_q=th[0, -1])
+    assert at["terms"][0, 4] == base["terms"][0, 4]
+    assert np.array_equal(at["grad"], base["grad"])
+    d = 0.07
+    gq = th[0, -1].copy()
+    gq[2] += d
+    off = oracle_mod.evaluate(rb, w, q0, goal7, th, p, goal_q=gq)
+    expect = 5000.0 * np.log(np.cosh(50.0 * d * d))
+    assert off["terms"][0, 4] - base["terms"][0, 4] == pytest.approx(expect, rel=1e-12)
+    # its gradient only touches theta_H, along the offset joint, pulling toward the goal
+    dg = off["grad"] - base["grad"]
+    assert np.all(dg[0, :-1] == 0.0)
+    assert dg[0, -1, 2] == pytest.approx(-2.0 * 5000.0 * 50.0 * np.tanh(50.0 * d * d) * d, rel=1e-9)
+    assert np.count_nonzero(dg[0, -1]) == 1
+
+
+def test_cspace_goal_gradient_finite_differences(oracle_mod):
+    from paper_2310_17274_gb300 import synth
+    rb = synth.make_robot(synth.SPHERES_42, seed=0)
+    w = synth.make_world(4, 1)
+    H = 6
+    rng = np.random.default_rng(4)
+    th = rng.uniform(-0.6, 0.6, size=(1, H, rb.dof))
+    q0 = rng.uniform(-0.6, 0.6, size=rb.dof)
+    gq = rng.uniform(-0.6, 0.6, size=rb.dof)
+    goal7 = np.array([0.3, 0.1, 0.4, 1.0, 0.0, 0.0, 0.0])
+    p = dict(flags=oracle_mod.params_default()["flags"] | oracle_mod.CSPACE_GOAL)
+    ref = oracle_mod.evaluate(rb, w, q0, goal7, th, p, goal_q=gq)
+    h = 1e-6
+    for j in range(rb.dof):
+        tp, tm = th.copy(), th.copy()
+        tp[0, -1, j] += h
+        tm[0, -1, j] -= h
+        fd = (oracle_mod.evaluate(rb, w, q0, goal7, tp, p, goal_q=gq)["cost"][0] -
+              oracle_mod.evaluate(rb, w, q0, goal7, tm, p, goal_q=gq)["cost"][0]) / (2 * h)
+        assert fd == pytest.approx(ref["grad"][0, -1, j], rel=2e-5, abs=1e-4)
