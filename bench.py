@@ -271,7 +271,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="crgb")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="ik,uneven,plain,serve,particle")
+    ap.add_argument("--extras", default="ik,uneven,plain,serve,particle,linesearch")
     ap.add_argument("--serve-rates", default="500,100")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--profile", type=int, default=0,
@@ -433,6 +433,8 @@ def main():
         extras["ik_no_collision"] = bench_ik(crgb, synth, ctx, R, rb, collision=False)
     if rank == 0 and "particle" in want:
         extras["particle"] = bench_particle(crgb, synth, ctx, R, rb, world, pr, P, iters)
+    if rank == 0 and "linesearch" in want:
+        extras["line_search"] = bench_line_search(crgb, synth, ctx, R, world, pr, iters)
     if rank == 0 and "uneven" in want:
         extras["uneven"] = bench_uneven(crgb, synth, ctx, R, rb)
     if rank == 0 and "serve" in want:
@@ -603,6 +605,43 @@ def bench_particle(crgb, synth, ctx, R, rb, world, pr, P, iters, n_particles=16,
     out.update({"particles_per_seed": n_particles, "particle_iters": n_iters, "beta": beta,
                 "k_mu": k_mu, "k_sigma": k_sigma, "sigma0": sigma0,
                 "samples": "unit Gaussian end offset per joint, ramped linearly over the horizon"})
+    return out
+
+
+def bench_line_search(crgb, synth, ctx, R, world, pr, iters):
+    """Line-search variants of Sec. 7.3 on the trajectory workload (same seeds,
+    same iterations): noisy-ls (the default), noisy-ls-1, Wolfe and strong
+    Wolfe over 12 step sizes with a 0.0 fallback, and no line search."""
+    import torch
+    W = crgb.World(world)
+    B, H, D = pr.seeds.shape
+    spec = crgb.ProblemSpec(W, pr.q_start, pr.goal, H, seeds=pr.seeds)
+    wolfe12 = [0.0, 1e-4, 1e-3, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0]
+    base = crgb.params_default()["flags"] & ~(crgb.WOLFE | crgb.STRONG_WOLFE)
+    variants = {
+        "noisy-ls": dict(alpha=[0.01, 0.3, 0.7, 1.0], flags=base | crgb.WOLFE),
+        "noisy-ls-1": dict(alpha=[0.01, 1.0], flags=base | crgb.WOLFE),
+        "wolfe": dict(alpha=wolfe12, flags=base | crgb.WOLFE),
+        "st-wolfe": dict(alpha=wolfe12, flags=base | crgb.WOLFE | crgb.STRONG_WOLFE),
+        "no-ls": dict(alpha=[1.0], flags=base),
+    }
+    out = {}
+    for name, p in variants.items():
+        P = crgb.make_params(p)
+        o = None
+        for _ in range(2):
+            o = crgb.solve(ctx, R, [spec], P, iters=iters, graph=True, persistent=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        o = crgb.solve(ctx, R, [spec], P, iters=iters, graph=True, persistent=True)[0]
+        e1.record()
+        torch.cuda.synchronize()
+        c = o.cost.cpu().numpy()
+        f = o.cfree.cpu().numpy().astype(bool)
+        out[name] = {"step_sizes": len(p["alpha"]), "ms": e0.elapsed_time(e1),
+                     "best_cost": float(c[int(o.best)]), "median_seed_cost": float(np.median(c)),
+                     "collision_free_seeds": int(f.sum())}
     return out
 
 

@@ -57,6 +57,7 @@ typedef int32_t cr_status;
 #define CR_STRONG_WOLFE 16u  /* strong Wolfe instead of weak */
 #define CR_IK_MODE 32u       /* single-state problems: no stencil terms, no sweep, no speed */
 #define CR_VEL_COST 64u      /* velocity log-cosh term of Eq. 16 on every sample */
+#define CR_CSPACE_GOAL 128u  /* joint-space goal cost of Eq. 15 (problems with goal_q) */
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* cr_last_error(void);
@@ -123,9 +124,11 @@ typedef struct {
   float alpha[CR_MAX_ALPHA];     /* step sizes; alpha[0] is the fallback "noisy" step */
   float armijo_c1, wolfe_c2;
   uint32_t flags;                /* CR_* flags above */
+  float w_cspace, k_cspace;      /* alpha_4, alpha_5 of Eq. 15 (with CR_CSPACE_GOAL) */
 } cr_params;
 
 /* Defaults: the paper's weights and constants (App. A.1-A.3, App. B.3:
+ * alpha_4 = 5000, alpha_5 = 50 for Eq. 15;
  * eta = 2.5 cm, weight 5000 for soft constraints; Sec. 7.3 step sizes
  * 0.01, 0.3, 0.7, 1.0), dt = 0.05, sweep_steps = 4, history = 6,
  * c1 = 1e-4, c2 = 0.9, flags = SWEPT|SPEED|SELF|WOLFE. */
@@ -139,6 +142,7 @@ typedef struct {
   int32_t n_seeds;            /* B */
   int32_t horizon;            /* H free timesteps theta_1..theta_H */
   const float* seeds;         /* [B][H][dof] host initial trajectories (cr_solve only) */
+  const float* goal_q;        /* [dof] host goal configuration for Eq. 15, or NULL */
 } cr_problem;
 
 /* ------------------------------------------------------------------------- */

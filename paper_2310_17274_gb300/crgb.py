@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libcrgb.so")
 _lock = threading.Lock()
 _lib = None
 
-SWEPT, SPEED, SELF, WOLFE, STRONG_WOLFE, IK_MODE, VEL_COST = 1, 2, 4, 8, 16, 32, 64
+SWEPT, SPEED, SELF, WOLFE, STRONG_WOLFE, IK_MODE, VEL_COST, CSPACE_GOAL = 1, 2, 4, 8, 16, 32, 64, 128
 N_TERMS = 5
 MAX_ALPHA = 16
 
@@ -50,12 +50,13 @@ class Params(C.Structure):
                 ("k_vel", C.c_float), ("eta", C.c_float), ("eta_bound", C.c_float),
                 ("dt", C.c_float), ("sweep_steps", C.c_int32), ("history", C.c_int32),
                 ("n_alpha", C.c_int32), ("alpha", C.c_float * MAX_ALPHA),
-                ("armijo_c1", C.c_float), ("wolfe_c2", C.c_float), ("flags", C.c_uint32)]
+                ("armijo_c1", C.c_float), ("wolfe_c2", C.c_float), ("flags", C.c_uint32),
+                ("w_cspace", C.c_float), ("k_cspace", C.c_float)]
 
 
 class Problem(C.Structure):
     _fields_ = [("world", _vp), ("q_start", _fp), ("goal", _fp), ("n_seeds", C.c_int32),
-                ("horizon", C.c_int32), ("seeds", _fp)]
+                ("horizon", C.c_int32), ("seeds", _fp), ("goal_q", _fp)]
 
 
 class Result(C.Structure):
@@ -244,17 +245,18 @@ def make_params(over: dict | None = None) -> Params:
 class ProblemSpec:
     """Host-side arrays of one problem, kept alive for the ctypes struct."""
 
-    def __init__(self, world: World, q_start, goal, horizon: int, seeds=None):
+    def __init__(self, world: World, q_start, goal, horizon: int, seeds=None, goal_q=None):
         self.world = world
         self.q_start = _f32(q_start)
         self.goal = _f32(goal)
         self.horizon = int(horizon)
         self.seeds = None if seeds is None else _f32(seeds)
+        self.goal_q = None if goal_q is None else _f32(goal_q)
 
     def struct(self) -> Problem:
         B = 0 if self.seeds is None else int(self.seeds.shape[0])
         return Problem(self.world.handle, _p(self.q_start), _p(self.goal), B, self.horizon,
-                       _p(self.seeds))
+                       _p(self.seeds), _p(self.goal_q))
 
 
 # ---------------------------------------------------------------------------

@@ -77,6 +77,8 @@ void cr_params_default(cr_params* p) {
   p->armijo_c1 = 1e-4f;
   p->wolfe_c2 = 0.9f;
   p->flags = CR_SWEPT | CR_SPEED | CR_SELF | CR_WOLFE;
+  p->w_cspace = 5000.f;  // alpha_4, App. A.1 (Eq. 15)
+  p->k_cspace = 50.f;    // alpha_5
 }
 
 cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
@@ -331,6 +333,10 @@ cr_status fill_problem(const cr_robot* rb, const cr_problem* pr, ProblemView* pv
   double R[9];
   if (!quat_rot(pr->goal + 3, R)) return fail(CR_EINVAL, "goal: degenerate quaternion");
   for (int k = 0; k < 9; ++k) pv->goal_R[k] = (float)R[k];
+  if (pr->goal_q) {
+    pv->has_goal_q = 1;
+    for (int j = 0; j < rb->dof; ++j) pv->goal_q[j] = pr->goal_q[j];
+  }
   return CR_OK;
 }
 

@@ -81,6 +81,8 @@ struct ProblemView {
   float q_start[kMaxDof];
   float goal_p[3];
   float goal_R[9];     // row-major
+  float goal_q[kMaxDof];  // Eq. 15 goal configuration when has_goal_q
+  int has_goal_q;
 };
 
 // Arguments of the fused evaluation kernel.

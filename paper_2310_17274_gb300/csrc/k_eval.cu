@@ -440,9 +440,22 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
         const V3 Gc = fr * v3(s_prob.goal_R[cc], s_prob.goal_R[3 + cc], s_prob.goal_R[6 + cc]);
         w = w + cross(Rc, Gc);
       }
+      // Eq. 15 joint-space goal term: alpha_4 logcosh(alpha_5 |theta_g - theta_H|^2);
+      // its gradient on theta_H is cq (theta_H - theta_g), cq kept beside the pose
+      float cq = 0.f;
+      if ((flags & CR_CSPACE_GOAL) && s_prob.has_goal_q) {
+        const float* thH = s_th + (r * H + H - 1) * D;
+        float r2 = 0.f;
+        for (int j = 0; j < D; ++j) {
+          const float d = thH[j] - s_prob.goal_q[j];
+          r2 = fmaf(d, d, r2);
+        }
+        s_goal[r] += prm.w_cspace * logcoshf(prm.k_cspace * r2);
+        cq = 2.f * prm.w_cspace * prm.k_cspace * tanhf(prm.k_cspace * r2);
+      }
       s_ee[3 * r] = make_float4(dp.x, dp.y, dp.z, 0.f);
       s_ee[3 * r + 1] = make_float4(w.x, w.y, w.z, 0.f);
-      s_ee[3 * r + 2] = make_float4(E[3], E[7], E[11], 0.f);
+      s_ee[3 * r + 2] = make_float4(E[3], E[7], E[11], cq);
     }
     __syncthreads();
 
@@ -892,6 +905,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
       float sl;
       bound_cost(s_th[k], s_lim[j], s_lim[D + j], e2, inv_e2, sl);
       float g = s_gth[k] + prm.w_bound * sl;
+      if (t == H) g = fmaf(s_ee[3 * r + 2].w, s_th[k] - s_prob.goal_q[j], g);  // Eq. 15
       if (!ik) {
         const int nhi = t == H ? H + 4 : t + 2;
         for (int n = t + 2; n <= nhi; ++n) {

@@ -31,10 +31,10 @@ def _lib():
     assert torch.cuda.is_available()
 
 
-def _gpu_eval(rb, w, pr, theta, params=None):
+def _gpu_eval(rb, w, pr, theta, params=None, goal_q=None):
     R = crgb.Robot(rb)
     W = crgb.World(w)
-    spec = crgb.ProblemSpec(W, pr.q_start, pr.goal, theta.shape[1])
+    spec = crgb.ProblemSpec(W, pr.q_start, pr.goal, theta.shape[1], goal_q=goal_q)
     out = crgb.evaluate(R, spec, torch.tensor(theta, dtype=torch.float32, device="cuda"), params)
     torch.cuda.synchronize()
     return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
@@ -118,6 +118,31 @@ def test_eval_parity_flags(flags):
     gpu = _gpu_eval(rb, w, pr, theta, p)
     ref = oracle.evaluate(rb, w, pr.q_start, pr.goal, theta, p)
     compare(gpu, ref, label=f"flags={flags}")
+
+
+@pytest.mark.parametrize("horizon,ik", [(32, False), (1, True)])
+def test_eval_parity_cspace_goal(horizon, ik):
+    """Eq. 15 joint-space goal cost at the last state (trajectories and IK)."""
+    rb, w, pr = scene(n_boxes=6, n_seeds=4, horizon=horizon, world_seed=5, problem_seed=6)
+    rng = np.random.default_rng(7)
+    # a goal pose away from every last state: near a reached pose the Eq. 14
+    # cost is steep in the end-effector position and FP32 kinematics error
+    # shows; Eq. 15 is what this test is about
+    pr.goal = f32(oracle.goal_pose_from_fk(rb, synth.uniform_config(rng, rb)))
+    goal_q = f32(pr.seeds[0, -1] + rng.normal(0, 0.3, size=rb.dof))
+    theta = line_search_batch(pr, rng, scale=0.1)
+    flags = (crgb.IK_MODE | crgb.SELF if ik else crgb.SWEPT | crgb.SPEED | crgb.SELF) | crgb.WOLFE
+    p = dict(flags=flags | crgb.CSPACE_GOAL)
+    gpu = _gpu_eval(rb, w, pr, theta, p, goal_q=goal_q)
+    ref = oracle.evaluate(rb, w, pr.q_start, pr.goal, theta, p, goal_q=goal_q)
+    n_cmp, _ = compare(gpu, ref, label=f"cspace H={horizon}")
+    assert n_cmp >= len(theta) // 2
+    # the flag without a goal configuration, and a goal configuration without the flag, add nothing
+    plain = oracle.evaluate(rb, w, pr.q_start, pr.goal, theta, dict(flags=flags))
+    g1 = _gpu_eval(rb, w, pr, theta, p)
+    g2 = _gpu_eval(rb, w, pr, theta, dict(flags=flags), goal_q=goal_q)
+    compare(g1, plain, label="flag only")
+    compare(g2, plain, label="goal only")
 
 
 def test_eval_parity_trajopt_shape():
