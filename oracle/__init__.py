@@ -110,6 +110,10 @@ def lib():
         L.cro_lbfgs_direction.argtypes = [C.POINTER(_Lbfgs), _dp]
         L.cro_ls_candidates.argtypes = [C.POINTER(_Params), C.c_int32, C.c_int32, _dp, _dp,
                                         _dp, _dp, _dp]
+        L.cro_steer_steps.argtypes = [C.c_int32, C.c_int32, _dp, C.c_double]
+        L.cro_steer_steps.restype = C.c_int32
+        L.cro_steer.argtypes = [C.POINTER(_Robot), C.POINTER(_World), C.c_int32, _dp, C.c_int32, _ip,
+                                _dp, _dp]
         L.cro_particle_sample.argtypes = [C.c_int32, C.c_int32, _dp, _dp, _dp, _dp]
         L.cro_particle_update.argtypes = [C.c_int32, C.c_int32, _dp, _dp, C.c_double, C.c_double,
                                           C.c_double, _dp, _dp, _dp]
@@ -437,3 +441,27 @@ def particle_update(cost, particles, mu, sigma, beta, k_mu, k_sigma):
     lib().cro_particle_update(n, n_p, _p(cost), _p(particles), float(beta), float(k_mu),
                               float(k_sigma), _p(mu), _p(sigma), _p(w))
     return mu, sigma, w
+
+
+# ---------------------------------------------------------------------------
+# Sec. 5 parallel steering
+# ---------------------------------------------------------------------------
+
+def steer_steps(edges, r):
+    """n of Alg. "Parallel Steering" for edges [E, 2, dof] at resolution r."""
+    e = _f64(edges)
+    return int(lib().cro_steer_steps(e.shape[0], e.shape[2], _p(e), float(r)))
+
+
+def steer(rb, world, edges, n):
+    """Last valid sample index, last valid configuration and its distance per edge."""
+    keep = _Keep()
+    R = _robot(rb, keep)
+    W = _world(world, keep)
+    e = _f64(edges)
+    E, _, dof = e.shape
+    last = np.zeros(E, dtype=np.int32)
+    v = np.zeros((E, dof))
+    d = np.zeros(E)
+    lib().cro_steer(C.byref(R), C.byref(W), E, _p(e), int(n), _p(last, _ip), _p(v), _p(d))
+    return last, v, d

@@ -883,3 +883,51 @@ void cro_particle_update(int32_t n, int32_t n_p, const double* cost, const doubl
   if (w) memcpy(w, wt, (size_t)n_p * sizeof(double));
   free(wt);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 5 Alg. "Parallel Steering"                                            */
+/* ------------------------------------------------------------------------ */
+
+int32_t cro_steer_steps(int32_t E, int32_t dof, const double* edges, double r) {
+  double gmax = 0.0;
+  for (int32_t e = 0; e < E; ++e)
+    for (int32_t j = 0; j < dof; ++j) {
+      double g = fabs(edges[((size_t)e * 2 + 1) * dof + j] - edges[((size_t)e * 2) * dof + j]);
+      if (g > gmax) gmax = g;
+    }
+  return (int32_t)floor(gmax / r) + 1;
+}
+
+void cro_steer(const cro_robot* rb, const cro_world* w, int32_t E, const double* edges, int32_t n,
+               int32_t* last, double* v_new, double* dist) {
+  const int D = rb->dof;
+  cro_params prm;
+  cro_params_default(&prm);
+  prm.flags = CRO_IK_MODE | CRO_SELF; /* single states: the discrete test only */
+  const double goal7[7] = {0, 0, 0, 1, 0, 0, 0};
+  double* l = (double*)malloc((size_t)D * sizeof(double));
+  for (int32_t e = 0; e < E; ++e) {
+    const double* a = edges + (size_t)e * 2 * D;
+    const double* b = a + D;
+    int32_t h = n;
+    for (int32_t i = 0; i <= n; ++i) {
+      for (int j = 0; j < D; ++j) l[j] = a[j] + ((double)i / n) * (b[j] - a[j]);
+      double c;
+      uint8_t ok;
+      cro_eval(rb, w, l, goal7, NULL, &prm, 1, l, 1, &c, NULL, &ok, NULL, NULL);
+      if (!ok) {
+        h = i - 1;
+        break;
+      }
+    }
+    last[e] = h;
+    double s = h < 0 ? 0.0 : (double)h / n, d2 = 0.0;
+    for (int j = 0; j < D; ++j) {
+      double v = a[j] + s * (b[j] - a[j]);
+      v_new[(size_t)e * D + j] = v;
+      d2 += (v - a[j]) * (v - a[j]);
+    }
+    dist[e] = sqrt(d2);
+  }
+  free(l);
+}

@@ -199,6 +199,25 @@ void cro_particle_update(int32_t n, int32_t n_p, const double* cost, const doubl
                          double beta, double k_mu, double k_sigma, double* mu, double* sigma,
                          double* w);
 
+/* ------------------------------------------------------------------------ */
+/* Sec. 5 Alg. "Parallel Steering": discretise each edge e = [theta_0,        */
+/* theta_1] into n + 1 samples l_i = theta_0 + (i / n)(theta_1 - theta_0),    */
+/* i = 0..n, check every sample (mask_samples: the discrete clearance test of */
+/* the evaluation, every sphere clear of every box and every pair of S        */
+/* separated), and keep the last valid sample before the first invalid one.   */
+/* ------------------------------------------------------------------------ */
+
+/* n of the algorithm: the largest joint displacement of any edge over the
+ * resolution r, floored, plus one.  edges [E][2][dof]. */
+int32_t cro_steer_steps(int32_t E, int32_t dof, const double* edges, double r);
+
+/* For each edge: last [E] = index of the last valid sample before the first
+ * invalid one (n when every sample is valid, -1 when sample 0 is invalid);
+ * v_new [E][dof] = that sample (theta_0 when last = -1); dist [E] = its
+ * Euclidean joint-space distance from theta_0. */
+void cro_steer(const cro_robot* rb, const cro_world* w, int32_t E, const double* edges, int32_t n,
+               int32_t* last, double* v_new, double* dist);
+
 #ifdef __cplusplus
 }
 #endif

@@ -852,3 +852,68 @@ def test_cspace_goal_gradient_finite_differences(oracle_mod):
         fd = (oracle_mod.evaluate(rb, w, q0, goal7, tp, p, goal_q=gq)["cost"][0] -
               oracle_mod.evaluate(rb, w, q0, goal7, tm, p, goal_q=gq)["cost"][0]) / (2 * h)
         assert fd == pytest.approx(ref["grad"][0, -1, j], rel=2e-5, abs=1e-4)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 5 Alg. "Parallel Steering"
+# ---------------------------------------------------------------------------
+
+def test_steer_steps_closed_form(oracle_mod):
+    edges = np.zeros((3, 2, 7))
+    edges[0, 1, 2] = 0.95
+    edges[1, 1, 4] = -0.31
+    edges[2, 0, 6] = 0.5
+    assert oracle_mod.steer_steps(edges, 0.1) == 10          # floor(9.5) + 1
+    assert oracle_mod.steer_steps(edges[1:2], 0.1) == 4       # floor(3.1) + 1
+
+
+def _first_invalid_brute_force(oracle_mod, rb, w, a, b, n):
+    """Per-sample clearance from the kinematics and the box distance alone."""
+    for i in range(n + 1):
+        q = a + (i / n) * (b - a)
+        _, sp, _ = oracle_mod.fk(rb, q)
+        for k in range(w.n):
+            for s in range(len(sp)):
+                if sp[s, 3] < 0:
+                    continue
+                if not (oracle_mod.box_sdf(w.pose[k], w.half_ext[k], sp[s, :3])[0] - sp[s, 3] > 0):
+                    return i
+        for (i1, j1) in rb.pairs:
+            if np.linalg.norm(sp[i1, :3] - sp[j1, :3]) - sp[i1, 3] - sp[j1, 3] <= 0:
+                return i
+    return n + 1
+
+
+def test_steer_free_edge_and_box_on_the_way(oracle_mod):
+    from paper_2310_17274_gb300 import synth
+    rb = synth.make_robot(synth.SPHERES_42, seed=0)
+    a = np.array([0.0, 0.3, 0.0, -0.4, 0.0, 0.2, 0.0])
+    b = np.array([1.2, -0.2, 0.5, 0.3, -0.6, 0.9, 0.4])
+    edges = np.stack([a, b])[None]
+    n = oracle_mod.steer_steps(edges, 0.05)
+    empty = synth.World(pose=np.zeros((0, 7)), half_ext=np.zeros((0, 3)))
+    assert _first_invalid_brute_force(oracle_mod, rb, empty, a, b, n) == n + 1, "self-colliding edge"
+    last, v, d = oracle_mod.steer(rb, empty, edges, n)
+    assert last[0] == n and np.allclose(v[0], b) and d[0] == pytest.approx(np.linalg.norm(b - a))
+    # a small box centred on the end effector's sphere at 60 % of the way
+    i_star = int(0.6 * n)
+    _, sp, _ = oracle_mod.fk(rb, a + (i_star / n) * (b - a))
+    s = int(np.argmax(np.where(rb.sphere_link == rb.dof - 1, 1, 0)))
+    w = synth.World(pose=np.array([[*sp[s, :3], 1.0, 0.0, 0.0, 0.0]]), half_ext=np.full((1, 3), 0.02))
+    first = _first_invalid_brute_force(oracle_mod, rb, w, a, b, n)
+    assert 0 < first <= i_star
+    last, v, d = oracle_mod.steer(rb, w, edges, n)
+    assert last[0] == first - 1
+    assert np.allclose(v[0], a + (last[0] / n) * (b - a))
+    assert d[0] == pytest.approx(np.linalg.norm(v[0] - a))
+
+
+def test_steer_start_in_collision(oracle_mod):
+    from paper_2310_17274_gb300 import synth
+    rb = synth.make_robot(synth.SPHERES_42, seed=0)
+    a = np.zeros(7)
+    b = np.full(7, 0.3)
+    _, sp, _ = oracle_mod.fk(rb, a)
+    w = synth.World(pose=np.array([[*sp[10, :3], 1.0, 0.0, 0.0, 0.0]]), half_ext=np.full((1, 3), 0.05))
+    last, v, d = oracle_mod.steer(rb, w, np.stack([a, b])[None], 5)
+    assert last[0] == -1 and np.array_equal(v[0], a) and d[0] == 0.0
