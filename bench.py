@@ -271,7 +271,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="crgb")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="ik,uneven,plain,serve,particle,linesearch")
+    ap.add_argument("--extras", default="ik,uneven,plain,serve,particle,linesearch,steer")
     ap.add_argument("--serve-rates", default="500,100")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--profile", type=int, default=0,
@@ -435,6 +435,8 @@ def main():
         extras["particle"] = bench_particle(crgb, synth, ctx, R, rb, world, pr, P, iters)
     if rank == 0 and "linesearch" in want:
         extras["line_search"] = bench_line_search(crgb, synth, ctx, R, world, pr, iters)
+    if rank == 0 and "steer" in want:
+        extras["steer"] = bench_steer(crgb, synth, R, rb, world)
     if rank == 0 and "uneven" in want:
         extras["uneven"] = bench_uneven(crgb, synth, ctx, R, rb)
     if rank == 0 and "serve" in want:
@@ -643,6 +645,33 @@ def bench_line_search(crgb, synth, ctx, R, world, pr, iters):
                      "best_cost": float(c[int(o.best)]), "median_seed_cost": float(np.median(c)),
                      "collision_free_seeds": int(f.sum())}
     return out
+
+
+def bench_steer(crgb, synth, R, rb, world, n_edges=4096, r=0.05):
+    """Sec. 5 parallel steering: n_edges random edges (ends within the limits,
+    joint steps N(0, 0.6^2)) in the trajectory workload's world, n + 1
+    samples each at resolution r: edges and samples checked per second."""
+    import torch
+    rng = np.random.default_rng(12)
+    a = synth.uniform_config(rng, rb, n_edges)
+    b = np.clip(a + rng.normal(0, 0.6, size=a.shape), rb.q_lo, rb.q_hi)
+    ed = torch.tensor(np.stack([a, b], axis=1), dtype=torch.float32, device="cuda")
+    n = crgb.steer_steps(ed, r)
+    W = crgb.World(world)
+    for _ in range(3):
+        out = crgb.steer(R, W, ed, n)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        out = crgb.steer(R, W, ed, n)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / 10
+    last = out["last"].cpu().numpy()
+    return {"edges": n_edges, "samples_per_edge": n + 1, "ms": t * 1e3, "edges_per_s": n_edges / t,
+            "samples_per_s": n_edges * (n + 1) / t, "fully_valid_edges": int((last == n).sum()),
+            "start_invalid_edges": int((last < 0).sum())}
 
 
 def bench_uneven(crgb, synth, ctx, R, rb, iters=100):

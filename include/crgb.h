@@ -244,6 +244,25 @@ cr_status cr_particle_step(const cr_robot* robot, const cr_problem* problem, con
                            const float* eps, float* particles, float* cost, float beta, float k_mu,
                            float k_sigma, void* stream);
 
+/* Parallel steering (Sec. 5, Alg. "Parallel Steering"), the edge check of
+ * the paper's geometric planner on the same kinematics and distance code:
+ * each edge e = [theta_0, theta_1] is discretised into n + 1 samples
+ * l_i = theta_0 + (i / n)(theta_1 - theta_0), i = 0..n (the algorithm's
+ * n = floor(max |theta_1 - theta_0| / r) + 1 is the caller's choice), every
+ * sample is checked as cr_eval's collision-free flag checks a state (every
+ * sphere clear of every box, every pair of S separated), and per edge:
+ *   last   device [E] int32: the last valid sample before the first invalid
+ *          one; n when all are valid, -1 when sample 0 is invalid
+ *   v_new  device [E][dof]: that sample (theta_0 when last = -1)
+ *   dist   device [E]: |v_new - theta_0| in joint space
+ *   edges  device [E][2][dof]; samples device [E][n+1][dof], valid device
+ *          [E][n+1] (uint8) and cost device [E][n+1] are scratch that hold
+ *          the samples, their flags and their single-state costs on return.
+ * Three launches on `stream`. */
+cr_status cr_steer(const cr_robot* robot, const cr_world* world, int32_t n_edges, const float* edges,
+                   int32_t n, float* samples, uint8_t* valid, float* cost, int32_t* last, float* v_new,
+                   float* dist, void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Runtime: context, batched solve                                            */
 /* ------------------------------------------------------------------------- */

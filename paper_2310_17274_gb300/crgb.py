@@ -94,6 +94,7 @@ SIGNATURES = {
                   C.POINTER(Result), _vp], C.c_int32),
     "cr_particle_step": ([_vp, C.POINTER(Problem), C.POINTER(Params), C.c_int32, C.c_int32, _vp,
                           _vp, _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, _vp], C.c_int32),
+    "cr_steer": ([_vp, _vp, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int32),
     "cr_autotune": ([_vp, _vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), C.c_int32,
                      C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                      C.POINTER(C.c_float)], C.c_int32),
@@ -317,6 +318,32 @@ def particle_step(robot: Robot, problem: ProblemSpec, mu, sigma, eps, params=Non
                                  float(beta), float(k_mu), float(k_sigma), _stream(stream)),
           "cr_particle_step")
     return particles, cost
+
+
+def steer_steps(edges, r):
+    """n of the parallel-steering algorithm: floor(max joint displacement / r) + 1."""
+    import torch
+    g = (edges[:, 1] - edges[:, 0]).abs().max().item() if edges.shape[0] else 0.0
+    return int(np.floor(g / r)) + 1
+
+
+def steer(robot: Robot, world: World, edges, n, stream=None):
+    """cr_steer on edges (CUDA float32 [E, 2, dof]) with n + 1 samples each.
+    Returns dict(last, v_new, dist, valid)."""
+    import torch
+    edges = edges.contiguous()
+    E, D = edges.shape[0], edges.shape[2]
+    dev = edges.device
+    samples = torch.empty((E, n + 1, D), device=dev)
+    valid = torch.empty((E, n + 1), device=dev, dtype=torch.uint8)
+    cost = torch.empty((E, n + 1), device=dev)
+    last = torch.empty(E, device=dev, dtype=torch.int32)
+    v_new = torch.empty((E, D), device=dev)
+    dist = torch.empty(E, device=dev)
+    check(lib().cr_steer(robot.handle, world.handle, int(E), _dptr(edges), int(n), _dptr(samples),
+                         _dptr(valid), _dptr(cost), _dptr(last), _dptr(v_new), _dptr(dist),
+                         _stream(stream)), "cr_steer")
+    return dict(last=last, v_new=v_new, dist=dist, valid=valid)
 
 
 class OptBuffers:
