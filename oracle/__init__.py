@@ -110,6 +110,8 @@ def lib():
         L.cro_lbfgs_direction.argtypes = [C.POINTER(_Lbfgs), _dp]
         L.cro_ls_candidates.argtypes = [C.POINTER(_Params), C.c_int32, C.c_int32, _dp, _dp,
                                         _dp, _dp, _dp]
+        L.cro_retime.argtypes = [C.POINTER(_Robot), C.c_int32, _dp, _dp]
+        L.cro_retime.restype = C.c_double
         L.cro_steer_steps.argtypes = [C.c_int32, C.c_int32, _dp, C.c_double]
         L.cro_steer_steps.restype = C.c_int32
         L.cro_steer.argtypes = [C.POINTER(_Robot), C.POINTER(_World), C.c_int32, _dp, C.c_int32, _ip,
@@ -465,3 +467,15 @@ def steer(rb, world, edges, n):
     d = np.zeros(E)
     lib().cro_steer(C.byref(R), C.byref(W), E, _p(e), int(n), _p(last, _ip), _p(v), _p(d))
     return last, v, d
+
+
+# ---------------------------------------------------------------------------
+# App. "Time-step Discretization"
+# ---------------------------------------------------------------------------
+
+def retime(rb, q0, theta):
+    """dt that puts one trajectory theta [H, dof] at the robot's limits."""
+    keep = _Keep()
+    R = _robot(rb, keep)
+    th = _f64(theta)
+    return float(lib().cro_retime(C.byref(R), th.shape[0], _p(_f64(q0)), _p(th)))

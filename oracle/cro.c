@@ -931,3 +931,27 @@ void cro_steer(const cro_robot* rb, const cro_world* w, int32_t E, const double*
   }
   free(l);
 }
+
+/* ------------------------------------------------------------------------ */
+/* App. "Time-step Discretization": retime                                    */
+/* ------------------------------------------------------------------------ */
+
+double cro_retime(const cro_robot* rb, int32_t H, const double* q0, const double* theta) {
+  const int D = rb->dof, NS = H + 1;
+  double* v = (double*)malloc((size_t)NS * D * sizeof(double));
+  double* a = (double*)malloc((size_t)NS * D * sizeof(double));
+  double* j = (double*)malloc((size_t)NS * D * sizeof(double));
+  cro_stencil(H, D, q0, theta, 1.0, v, a, j);
+  double dt = 0.0;
+  for (int k = 0; k < NS * D; ++k) {
+    int jj = k % D;
+    double dv = fabs(v[k]) / rb->v_max[jj];
+    double da = sqrt(fabs(a[k]) / rb->a_max[jj]);
+    double dj = cbrt(fabs(j[k]) / rb->j_max[jj]);
+    if (dv > dt) dt = dv;
+    if (da > dt) dt = da;
+    if (dj > dt) dt = dj;
+  }
+  free(v); free(a); free(j);
+  return dt;
+}

@@ -218,6 +218,17 @@ int32_t cro_steer_steps(int32_t E, int32_t dof, const double* edges, double r);
 void cro_steer(const cro_robot* rb, const cro_world* w, int32_t E, const double* edges, int32_t n,
                int32_t* last, double* v_new, double* dist);
 
+/* ------------------------------------------------------------------------ */
+/* App. "Time-step Discretization" (Alg. "Time Discretization"): retime       */
+/* ------------------------------------------------------------------------ */
+
+/* The time step that puts a trajectory at the robot's limits: the App. A.5
+ * derivatives scale as 1/dt, 1/dt^2, 1/dt^3, so with v1, a1, j1 the stencils
+ * at dt = 1 the smallest dt keeping every sample within the limits is
+ * max over samples and joints of |v1|/v_max, sqrt(|a1|/a_max), cbrt(|j1|/j_max).
+ * theta [H][dof] (one trajectory), q0 the start configuration. */
+double cro_retime(const cro_robot* rb, int32_t H, const double* q0, const double* theta);
+
 #ifdef __cplusplus
 }
 #endif

@@ -917,3 +917,29 @@ def test_steer_start_in_collision(oracle_mod):
     w = synth.World(pose=np.array([[*sp[10, :3], 1.0, 0.0, 0.0, 0.0]]), half_ext=np.full((1, 3), 0.05))
     last, v, d = oracle_mod.steer(rb, w, np.stack([a, b])[None], 5)
     assert last[0] == -1 and np.array_equal(v[0], a) and d[0] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# App. "Time-step Discretization": retime
+# ---------------------------------------------------------------------------
+
+def test_retime_scaling_and_limits(oracle_mod):
+    """A trajectory retimed to dt is at the limit at dt: the largest of the
+    velocity, acceleration and jerk ratios (App. A.5 stencils at dt) is 1; a
+    constant trajectory needs no time at all."""
+    from paper_2310_17274_gb300 import synth
+    rb = synth.make_robot(synth.SPHERES_42, seed=0)
+    H = 20
+    rng = np.random.default_rng(6)
+    q0 = rng.uniform(-0.3, 0.3, size=rb.dof)
+    th = q0 + np.cumsum(rng.normal(0, 0.05, size=(H, rb.dof)), axis=0)
+    dt = oracle_mod.retime(rb, q0, th)
+    v, a, j = oracle_mod.stencil(q0, th, dt)
+    ratio = max(np.max(np.abs(v) / rb.v_max), np.max(np.abs(a) / rb.a_max), np.max(np.abs(j) / rb.j_max))
+    assert ratio == pytest.approx(1.0, rel=1e-12)
+    # the same shape twice as large in every joint: each ratio grows by 2,
+    # so dt grows by 2, sqrt(2) or cbrt(2) depending on the binding limit
+    dt2 = oracle_mod.retime(rb, q0, q0 + 2.0 * (th - q0))
+    assert dt2 / dt == pytest.approx(2.0) or dt2 / dt == pytest.approx(np.sqrt(2.0)) or \
+        dt2 / dt == pytest.approx(np.cbrt(2.0))
+    assert oracle_mod.retime(rb, q0, np.tile(q0, (H, 1))) == 0.0
