@@ -942,4 +942,4 @@ def test_retime_scaling_and_limits(oracle_mod):
     dt2 = oracle_mod.retime(rb, q0, q0 + 2.0 * (th - q0))
     assert dt2 / dt == pytest.approx(2.0) or dt2 / dt == pytest.approx(np.sqrt(2.0)) or \
         dt2 / dt == pytest.approx(np.cbrt(2.0))
-    assert oracle_mod.retime(rb, q0, np.tile(q0, (H, 1))) == 0.0
+    assert oracle_mod.retime(rb, q0, np.tile(q0, (H, 1))) < 1e-6   # rounding residue only (cube root)
