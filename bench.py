@@ -271,7 +271,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="crgb")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="ik,uneven,plain,serve,particle,linesearch,steer")
+    ap.add_argument("--extras", default="ik,uneven,plain,serve,particle,linesearch,steer,timeopt")
     ap.add_argument("--serve-rates", default="500,100")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--profile", type=int, default=0,
@@ -437,6 +437,8 @@ def main():
         extras["line_search"] = bench_line_search(crgb, synth, ctx, R, world, pr, iters)
     if rank == 0 and "steer" in want:
         extras["steer"] = bench_steer(crgb, synth, R, rb, world)
+    if rank == 0 and "timeopt" in want:
+        extras["timeopt"] = bench_timeopt(crgb, synth, ctx, R, world, pr, dict(alpha=list(cfg.alphas)))
     if rank == 0 and "uneven" in want:
         extras["uneven"] = bench_uneven(crgb, synth, ctx, R, rb)
     if rank == 0 and "serve" in want:
@@ -672,6 +674,28 @@ def bench_steer(crgb, synth, R, rb, world, n_edges=4096, r=0.05):
     return {"edges": n_edges, "samples_per_edge": n + 1, "ms": t * 1e3, "edges_per_s": n_edges / t,
             "samples_per_s": n_edges * (n + 1) / t, "fully_valid_edges": int((last == n).sum()),
             "start_invalid_edges": int((last < 0).sum())}
+
+
+def bench_timeopt(crgb, synth, ctx, R, world, pr, P_over):
+    """Alg. "Time Discretization" on the trajectory workload: solve at dt 0.25
+    without jerk, retime, scale the weights, solve again with jerk, retime."""
+    import torch
+    W = crgb.World(world)
+    B, H, D = pr.seeds.shape
+    spec = crgb.ProblemSpec(W, pr.q_start, pr.goal, H, seeds=pr.seeds)
+    for _ in range(2):
+        crgb.time_discretized_solve(ctx, R, spec, P_over, iters=(100, 100))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out, dt_opt, dt_f = crgb.time_discretized_solve(ctx, R, spec, P_over, iters=(100, 100))
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    c = out.cost.cpu().numpy()
+    return {"ms": t * 1e3, "dt_opt": dt_opt, "dt_final": dt_f, "motion_time_s": H * dt_f,
+            "best_cost": float(c[int(out.best)]),
+            "collision_free_seeds": int(out.cfree.cpu().numpy().astype(bool).sum()),
+            "what": "two 100-iteration solves (dt 0.25 without jerk, then dt_opt) and two retimings, "
+                    "host round trips included"}
 
 
 def bench_uneven(crgb, synth, ctx, R, rb, iters=100):

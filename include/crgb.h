@@ -263,6 +263,15 @@ cr_status cr_steer(const cr_robot* robot, const cr_world* world, int32_t n_edges
                    int32_t n, float* samples, uint8_t* valid, float* cost, int32_t* last, float* v_new,
                    float* dist, void* stream);
 
+/* Retiming of App. "Time-step Discretization" (Alg. "Time Discretization"):
+ * for B trajectories theta (device [B][H][dof], H = problem->horizon, start
+ * problem->q_start) writes dt (device [B]), the time step that puts each at
+ * the robot's velocity, acceleration or jerk limit: the App. A.5 stencils at
+ * dt = 1 give v1, a1, j1 and dt = max over samples and joints of
+ * |v1|/v_max, sqrt(|a1|/a_max), cbrt(|j1|/j_max).  One launch on `stream`. */
+cr_status cr_retime(const cr_robot* robot, const cr_problem* problem, int32_t B, const float* theta,
+                    float* dt, void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Runtime: context, batched solve                                            */
 /* ------------------------------------------------------------------------- */

@@ -95,6 +95,7 @@ SIGNATURES = {
     "cr_particle_step": ([_vp, C.POINTER(Problem), C.POINTER(Params), C.c_int32, C.c_int32, _vp,
                           _vp, _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, _vp], C.c_int32),
     "cr_steer": ([_vp, _vp, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int32),
+    "cr_retime": ([_vp, C.POINTER(Problem), C.c_int32, _vp, _vp, _vp], C.c_int32),
     "cr_autotune": ([_vp, _vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), C.c_int32,
                      C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                      C.POINTER(C.c_float)], C.c_int32),
@@ -344,6 +345,54 @@ def steer(robot: Robot, world: World, edges, n, stream=None):
                          _dptr(valid), _dptr(cost), _dptr(last), _dptr(v_new), _dptr(dist),
                          _stream(stream)), "cr_steer")
     return dict(last=last, v_new=v_new, dist=dist, valid=valid)
+
+
+def retime(robot: Robot, problem: ProblemSpec, theta, stream=None):
+    """dt that puts each trajectory of theta (CUDA float32 [B, H, dof]) at the
+    robot's velocity, acceleration or jerk limit (cr_retime)."""
+    import torch
+    theta = theta.contiguous()
+    dt = torch.empty(theta.shape[0], device=theta.device)
+    pr = problem.struct()
+    check(lib().cr_retime(robot.handle, C.byref(pr), int(theta.shape[0]), _dptr(theta), _dptr(dt),
+                          _stream(stream)), "cr_retime")
+    return dt
+
+
+def time_discretized_solve(ctx, robot: Robot, problem: ProblemSpec, params=None, iters=(100, 100),
+                           dt_init=0.25):
+    """Alg. "Time Discretization" (App. "Time-step Discretization") for one
+    problem: solve at dt_init without the jerk term; retime the best seed to
+    dt_opt (the step that puts it at the limits); scale the derivative weights
+    to dt_opt and enable jerk; solve again from the first solution at dt_opt;
+    retime the result to dt_f.  Weights on the square of the k-th derivative
+    are multiplied by (dt / dt0)^(2k), dt0 the params' own dt, so each term
+    keeps the magnitude it has for the same trajectory at dt0 (the paper says
+    only that the weights are scaled by the new dt).
+    Returns (SolveOutput, dt_opt, dt_f)."""
+    base = params_default()
+    if params:
+        base.update(params if isinstance(params, dict) else {})
+    dt0 = float(base["dt"])
+
+    def scaled(dt, jerk):
+        p = dict(base)
+        r = dt / dt0
+        p["dt"] = dt
+        p["w_vel"] = base["w_vel"] * r ** 2
+        p["w_acc"] = base["w_acc"] * r ** 4
+        p["w_jerk"] = base["w_jerk"] * r ** 6 if jerk else 0.0
+        return make_params(p)
+
+    o1 = solve(ctx, robot, [problem], scaled(dt_init, False), iters=iters[0])[0]
+    b1 = int(o1.best)
+    dt_opt = float(retime(robot, problem, o1.traj[b1:b1 + 1])[0])
+    dt_opt = max(dt_opt, 1e-3)
+    o2 = solve(ctx, robot, [problem], scaled(dt_opt, True), iters=iters[1],
+               device_seeds=[o1.traj.contiguous()])[0]
+    b2 = int(o2.best)
+    dt_f = float(retime(robot, problem, o2.traj[b2:b2 + 1])[0])
+    return o2, dt_opt, dt_f
 
 
 class OptBuffers:
