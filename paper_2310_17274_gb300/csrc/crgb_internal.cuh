@@ -148,7 +148,11 @@ struct EvalSmem {
     off_sts = take(max_states * 4);
     off_sta = take(max_states * 4);
     off_gth = take(max_states * dof * 4);
-    off_wsph = take(store_x ? 0 : n_warps * M * 16);
+    {  // per-warp sphere positions of the self term (without the cache), then
+       // the world cost of each (state, sphere) in backward passes 1-2
+      const int wsph = store_x ? 0 : n_warps * M * 16, wc = max_states * M * 4;
+      off_wsph = take(wsph > wc ? wsph : wc);
+    }
     off_box = take(kBoxChunk * (int)sizeof(BoxRows));
     off_ee = take(max_traj * 48);
     // stencil samples of a tile: nt (H + 1) <= max_states + max_traj

@@ -243,6 +243,9 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   int* s_sta = reinterpret_cast<int*>(smem + L.off_sta);
   uint32_t* s_gmask = reinterpret_cast<uint32_t*>(smem + L.off_gmask);
   float4* s_wsph = reinterpret_cast<float4*>(smem + L.off_wsph);
+  // world cost of each (state, sphere) from backward pass 1, in the same
+  // region once the self term no longer needs it
+  float* s_wc = reinterpret_cast<float*>(smem + L.off_wsph);
   float* s_gth = reinterpret_cast<float*>(smem + L.off_gth);
   BoxRows* s_box = reinterpret_cast<BoxRows*>(smem + L.off_box);
   float4* s_ee = reinterpret_cast<float4*>(smem + L.off_ee);
@@ -781,6 +784,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
       g3[1] = gx.x;
       g3[2] = gx.y;
       g3[3] = gx.z;
+      s_wc[k] = wc;
       if (wc != 0.f || gx.x != 0.f || gx.y != 0.f || gx.z != 0.f)
         atomicOr(&s_nz[sg * MW + i / 32], 1u << (i % 32));
     };
@@ -831,15 +835,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
         while (bits) {
           const int i = w * 32 + __ffs(bits) - 1;
           bits &= bits - 1u;
-          if (j == 0 && K > 0) {
-            // world cost of the sphere: beta_2 speed S (recomputed, few spheres)
-            const float Si = s_sg[sg * M + i].x;
-            if (Si != 0.f) {
-              float v = 1.f;
-              if (speed) v = norm(pos(slot(r, t + 1), i) - pos(slot(r, t - 1), i)) * inv2dt;
-              wsum += prm.w_coll * v * Si;
-            }
-          }
+          // world cost of the sphere (beta_2 speed S, from backward pass 1)
+          if (j == 0 && K > 0 && s_sg[sg * M + i].x != 0.f) wsum += s_wc[sg * M + i];
           if (s_link[i] < j) continue;
           const float4 g = s_sg[sg * M + i];
           acc += dot(v3(g.y, g.z, g.w), cross(aj, pos(sl, i) - oj));
