@@ -818,36 +818,28 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
       for (int e = tid; e < n_list; e += nthr) bw1_item((int)s_list[e]);
     }
     __syncthreads();
-    // (2) per (state, joint): sum over the spheres on links at or after the
-    //     joint of gx . (a_j x (x - o_j)), in sphere order; the joint-0 thread
-    //     also adds up the state's world cost
+    // (2) Jacobian transpose in suffix form: joint j's sum over the spheres on
+    //     links at or after j of gx . (a_j x (x - o_j)) equals
+    //     a_j . (sum_{l >= j} P_l - o_j x sum_{l >= j} F_l) with, per link l,
+    //     P_l = sum x x gx and F_l = sum gx over its non-zero spheres.
+    // (2a) per (state, link): P_l and F_l in sphere order, in the region of the
+    //      link centres and box masks (unused since the collision terms)
+    float* s_pf = reinterpret_cast<float*>(smem + L.off_rho);  // [S][dof][6]
     for (int k = tid; k < S * D; k += nthr) {
-      const int sg = k / D, j = k % D;
-      const int r = sg / H, t = sg % H + 1;
-      const int sl = slot(r, t);
-      const float* T = s_lt + (sl * D + j) * 12;
-      const int ax = s_axis[j];
-      const V3 aj = v3(T[ax], T[4 + ax], T[8 + ax]);
-      const V3 oj = v3(T[3], T[7], T[11]);
-      float acc = 0.f, wsum = 0.f;
-      for (int w = 0; w < MW; ++w) {
-        uint32_t bits = s_nz[sg * MW + w];
-        while (bits) {
-          const int i = w * 32 + __ffs(bits) - 1;
-          bits &= bits - 1u;
-          // world cost of the sphere (beta_2 speed S, from backward pass 1)
-          if (j == 0 && K > 0 && s_sg[sg * M + i].x != 0.f) wsum += s_wc[sg * M + i];
-          if (s_link[i] < j) continue;
-          const float4 g = s_sg[sg * M + i];
-          acc += dot(v3(g.y, g.z, g.w), cross(aj, pos(sl, i) - oj));
-        }
+      const int sg = k / D, l = k % D;
+      const int sl = slot(sg / H, sg % H + 1);
+      V3 P = v3(0.f, 0.f, 0.f), F = v3(0.f, 0.f, 0.f);
+      for (int q = s_lst[l]; q < s_lst[l + 1]; ++q) {
+        const int i = s_lsp[q];
+        if (!((s_nz[sg * MW + (i >> 5)] >> (i & 31)) & 1u)) continue;
+        const float4 g = s_sg[sg * M + i];
+        const V3 gv = v3(g.y, g.z, g.w);
+        P = P + cross(pos(sl, i), gv);
+        F = F + gv;
       }
-      if (t == H) {
-        const float4 dp = s_ee[3 * r], w = s_ee[3 * r + 1], pe = s_ee[3 * r + 2];
-        acc += dot(v3(dp.x, dp.y, dp.z), cross(aj, v3(pe.x, pe.y, pe.z) - oj)) + dot(aj, v3(w.x, w.y, w.z));
-      }
-      s_gth[k] = acc;
-      if (j == 0) s_stw[sg] = wsum;
+      float* o = s_pf + 6 * k;
+      o[0] = P.x; o[1] = P.y; o[2] = P.z;
+      o[3] = F.x; o[4] = F.y; o[5] = F.z;
     }
 
     // ---- Eq. 17 position bound; App. A.5 stencils with Eq. 16 and Eq. 17 on v, a, j
@@ -892,6 +884,45 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
         s_sten[3 * k + 2] = dj;
         s_sm[k] = sm;
         s_db[k] = prm.w_bound * db;
+      }
+    }
+    __syncthreads();
+    // (2b) per (state, joint): the suffix sums and the end-effector terms; the
+    //      joint-0 item also adds up the state's world cost in sphere order
+    for (int k = tid; k < S * D; k += nthr) {
+      const int sg = k / D, j = k % D;
+      const int r = sg / H, t = sg % H + 1;
+      const int sl = slot(r, t);
+      const float* T = s_lt + (sl * D + j) * 12;
+      const int ax = s_axis[j];
+      const V3 aj = v3(T[ax], T[4 + ax], T[8 + ax]);
+      const V3 oj = v3(T[3], T[7], T[11]);
+      V3 Ps = v3(0.f, 0.f, 0.f), Fs = v3(0.f, 0.f, 0.f);
+      for (int l = j; l < D; ++l) {
+        const float* p = s_pf + 6 * (sg * D + l);
+        Ps = Ps + v3(p[0], p[1], p[2]);
+        Fs = Fs + v3(p[3], p[4], p[5]);
+      }
+      float acc = dot(aj, Ps) - dot(aj, cross(oj, Fs));
+      if (t == H) {
+        const float4 dp = s_ee[3 * r], w = s_ee[3 * r + 1], pe = s_ee[3 * r + 2];
+        acc += dot(v3(dp.x, dp.y, dp.z), cross(aj, v3(pe.x, pe.y, pe.z) - oj)) + dot(aj, v3(w.x, w.y, w.z));
+      }
+      s_gth[k] = acc;
+      if (j == 0) {
+        float wsum = 0.f;
+        if (K > 0) {
+          for (int w = 0; w < MW; ++w) {
+            uint32_t bits = s_nz[sg * MW + w];
+            while (bits) {
+              const int i = w * 32 + __ffs(bits) - 1;
+              bits &= bits - 1u;
+              // world cost of the sphere (beta_2 speed S, from backward pass 1)
+              if (s_sg[sg * M + i].x != 0.f) wsum += s_wc[sg * M + i];
+            }
+          }
+        }
+        s_stw[sg] = wsum;
       }
     }
     __syncthreads();
