@@ -211,7 +211,17 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
         }
       }
       float tot[CR_MAX_ALPHA + 1];
-      block_sum<NT, SLOTS, CR_MAX_ALPHA + 1>(v, tot, red, phase);
+      // only the first n_alpha + 1 sums are used: reduce 5 or 9 of them when
+      // that is enough (the sums themselves do not depend on how many)
+      if (na <= 4) {
+        block_sum<NT, SLOTS, 5>(reinterpret_cast<Part<NT, SLOTS>(&)[5]>(v),
+                                reinterpret_cast<float(&)[5]>(tot), red, phase);
+      } else if (na <= 8) {
+        block_sum<NT, SLOTS, 9>(reinterpret_cast<Part<NT, SLOTS>(&)[9]>(v),
+                                reinterpret_cast<float(&)[9]>(tot), red, phase);
+      } else {
+        block_sum<NT, SLOTS, CR_MAX_ALPHA + 1>(v, tot, red, phase);
+      }
       const float c0 = c_cur;
       const float gd0 = tot[0];
       int idx = 0;
