@@ -118,7 +118,8 @@ def _rot_to_quat(R):
 # those sources; any change to them reports traffic as null until recaptured.
 EVAL_TRAFFIC = {"bytes": 604160, "states": 12288, "sources_sha256": "33134884024c1fb1",
                 "profile": "profiles/k_eval_trajopt_32x48x8.md"}
-EVAL_SOURCES = ("paper_2310_17274_gb300/csrc/k_eval.cu", "paper_2310_17274_gb300/csrc/crgb_internal.cuh")
+EVAL_SOURCES = ("paper_2310_17274_gb300/csrc/k_eval.cu", "paper_2310_17274_gb300/csrc/crgb_internal.cuh",
+                "paper_2310_17274_gb300/csrc/k_device.cuh")
 
 
 def eval_traffic(states_per_launch):

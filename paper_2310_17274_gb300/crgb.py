@@ -254,11 +254,16 @@ class ProblemSpec:
         self.horizon = int(horizon)
         self.seeds = None if seeds is None else _f32(seeds)
         self.goal_q = None if goal_q is None else _f32(goal_q)
+        self._struct = None
 
     def struct(self) -> Problem:
-        B = 0 if self.seeds is None else int(self.seeds.shape[0])
-        return Problem(self.world.handle, _p(self.q_start), _p(self.goal), B, self.horizon,
-                       _p(self.seeds), _p(self.goal_q))
+        """The ctypes view of this problem, built once (the arrays it points
+        to live as long as this object)."""
+        if self._struct is None:
+            B = 0 if self.seeds is None else int(self.seeds.shape[0])
+            self._struct = Problem(self.world.handle, _p(self.q_start), _p(self.goal), B, self.horizon,
+                                   _p(self.seeds), _p(self.goal_q))
+        return self._struct
 
 
 # ---------------------------------------------------------------------------
@@ -466,9 +471,10 @@ class SolveOutput:
         self.cost = torch.empty(n_seeds, device=device)
         self.cfree = torch.empty(n_seeds, device=device, dtype=torch.uint8)
         self.best = torch.empty(1, device=device, dtype=torch.int32)
+        self._struct = Result(_dptr(self.traj), _dptr(self.cost), _dptr(self.cfree), _dptr(self.best))
 
     def struct(self) -> Result:
-        return Result(_dptr(self.traj), _dptr(self.cost), _dptr(self.cfree), _dptr(self.best))
+        return self._struct
 
 
 def solve(ctx: Context, robot: Robot, problems, params=None, iters=25, graph=True,
@@ -481,6 +487,7 @@ def solve(ctx: Context, robot: Robot, problems, params=None, iters=25, graph=Tru
     n = len(probs)
     structs = [p.struct() for p in probs]
     if device_seeds is not None:
+        structs = [Problem.from_buffer_copy(s) for s in structs]  # the cached views stay host-seeded
         for s, t in zip(structs, device_seeds):
             s.seeds = C.cast(C.c_void_p(t.data_ptr()), _fp)
             s.n_seeds = int(t.shape[0])

@@ -165,8 +165,19 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
     std::vector<int> fill(lstart.begin(), lstart.end() - 1);
     for (int i = 0; i < M; ++i) lsph[fill[d->sphere_link[i]]++] = i;
   }
+  // robots of up to 64 spheres: the grouped index of the pair {i, j} at [i][j]
+  // and [j][i] (the caller's first when listed twice), -1 when not a pair
+  const int n_at = M <= kPairTableSpheres && P <= 32767 ? M * M : 0;
+  std::vector<int16_t> pair_at((size_t)(n_at > 0 ? n_at : 1), (int16_t)-1);
+  for (int q = 0; q < P && n_at > 0; ++q) {
+    const int i = (int)(pairs[q] & 0xffffu), j = (int)(pairs[q] >> 16);
+    for (int side = 0; side < 2; ++side) {
+      int16_t& at = side == 0 ? pair_at[(size_t)i * M + j] : pair_at[(size_t)j * M + i];
+      if (at < 0 || orig[q] < orig[at]) at = (int16_t)q;
+    }
+  }
   // one blob: fixed_tf | lim | spheres (float4) | axis | link | offsets | link spheres | pairs |
-  // original positions | groups
+  // original positions | groups | pair table
   const size_t n_fix = (size_t)(D + 1) * 12, n_lim = (size_t)5 * D;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t r = off; off = (off + bytes + 255) & ~size_t(255); return r; };
@@ -175,7 +186,8 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
                o_soff = take((size_t)M * 4), o_lbs = take((size_t)D * 16), o_ldm = take((size_t)D * 4),
                o_pairs = take((size_t)(P > 0 ? P : 1) * 4), o_orig = take((size_t)(P > 0 ? P : 1) * 4),
                o_grp = take((size_t)(G > 0 ? G : 1) * 16), o_lst = take((size_t)(D + 1) * 4),
-               o_lsp = take((size_t)(M > 0 ? M : 1) * 4);
+               o_lsp = take((size_t)(M > 0 ? M : 1) * 4), o_pat = take(pair_at.size() * 2),
+               o_ls4 = take((size_t)(M > 0 ? M : 1) * 16);
   std::vector<unsigned char> host(off, 0);
   std::memcpy(host.data() + o_fix, d->fixed_tf, n_fix * 4);
   float* lim = reinterpret_cast<float*>(host.data() + o_lim);
@@ -199,6 +211,8 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
   if (G > 0) std::memcpy(host.data() + o_grp, groups.data(), (size_t)G * 16);
   std::memcpy(host.data() + o_lst, lstart.data(), (size_t)(D + 1) * 4);
   std::memcpy(host.data() + o_lsp, lsph.data(), (size_t)M * 4);
+  std::memcpy(host.data() + o_pat, pair_at.data(), pair_at.size() * 2);
+  for (int q = 0; q < M; ++q) std::memcpy(host.data() + o_ls4 + (size_t)q * 16, d->spheres + 4 * lsph[q], 16);
   void* dev = nullptr;
   cudaError_t e = cudaMalloc(&dev, off);
   if (e != cudaSuccess) return fail(CR_ENOMEM, "cudaMalloc(%zu): %s", off, cudaGetErrorString(e));
@@ -231,6 +245,8 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
   r->view.link_start = reinterpret_cast<const int*>(b + o_lst);
   r->view.link_sph = reinterpret_cast<const int*>(b + o_lsp);
   r->view.max_link_spheres = max_ls;
+  r->view.pair_at = n_at > 0 ? reinterpret_cast<const int16_t*>(b + o_pat) : nullptr;
+  r->view.link_sph4 = reinterpret_cast<const float4*>(b + o_ls4);
   for (int j = 0; j < D; ++j) {
     r->q_lo[j] = d->q_lo[j];
     r->q_hi[j] = d->q_hi[j];

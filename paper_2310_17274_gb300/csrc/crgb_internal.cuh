@@ -12,6 +12,7 @@ namespace crgb {
 constexpr int kMaxDof = CR_MAX_DOF;
 constexpr int kMaxSpheres = 1024;
 constexpr int kMaxPairs = 65535;
+constexpr int kPairTableSpheres = 64;  // robots up to this size get the pair table
 constexpr int kMaxBoxes = 4096;
 constexpr int kMaxHorizon = 128;
 constexpr int kBoxChunk = 64;  // boxes staged in shared memory at a time
@@ -60,7 +61,10 @@ struct RobotView {
   const int4* groups;       // [G] (link a, link b, first pair, pair count)
   const int* link_start;    // [dof+1] spheres of link l are link_sph[link_start[l] .. link_start[l+1])
   const int* link_sph;      // [M] sphere indices ordered by link
+  const float4* link_sph4;  // [M] the same spheres' centres and radii, in that order
   int max_link_spheres;     // largest sphere count of a link
+  const int16_t* pair_at;   // [M][M] grouped index of the pair {i, j} (caller's first when listed
+                            //   twice) or -1; robots of up to kPairTableSpheres spheres, else nullptr
 };
 
 // One box packed as five float4 rows: (R^T row k, t_k) for k = 0..2 so that
@@ -206,6 +210,11 @@ cudaError_t launch_eval(const EvalArgs& a, int grid, int block, cudaStream_t str
 int eval_smem_bytes(const EvalArgs& a, int block);
 int eval_blocks_per_sm(const EvalArgs& a, int block);
 int eval_smem_limit();  // largest dynamic shared memory a tile may use
+// IK mode (no sweep, speed or stencils): one thread per trajectory; launch_eval
+// and the two queries above route IK-mode arguments here
+cudaError_t launch_eval_ik(const EvalArgs& a, cudaStream_t stream);
+int eval_ik_smem_bytes(int dof);
+int eval_ik_blocks_per_sm(int dof);
 cudaError_t launch_opt(const OptArgs& a, int n_max, cudaStream_t stream);
 int opt_smem_bytes(int history, int n_max);
 

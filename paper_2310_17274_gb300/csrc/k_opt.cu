@@ -428,6 +428,213 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
   }
 }
 
+// Seeds of at most N <= 32 variables (IK, very short horizons), one thread
+// per seed.  A dot product is formed exactly as the one-warp kernel forms it
+// (lane k holds fma(a_k, b_k, 0) for k < n and +0 beyond; lane 0's xor
+// butterfly adds lane o's partial to its own for o = 16, 8, 4, 2, 1; the
+// virtual-warp sum is 0 + w_0 + 0 + ... + 0), and every element update is
+// the same fma, so a seed's result is bit-identical to k_opt<32, 1> and
+// hence to every other width.
+template <int N>
+__device__ __forceinline__ float lane_dot(const float (&a)[N], const float (&b)[N], int n) {
+  float p[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) p[k] = k < N && k < n ? fmaf(a[k < N ? k : 0], b[k < N ? k : 0], 0.f) : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int l = 0; l < o; ++l) p[l] = p[l] + p[l + o];
+  float s = 0.f;
+  s += p[0];
+#pragma unroll
+  for (int w = 1; w < kVirt / 32; ++w) s += 0.f;
+  return s;
+}
+
+template <int N>
+__device__ __forceinline__ void lane_load(float (&v)[N], const float* src, int n) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = k < n ? src[k] : 0.f;
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_opt_lane(const __grid_constant__ OptArgs a) {
+  const int D = a.dof, m = a.prm.history, na = a.prm.n_alpha;
+  const cr_opt_state& st = a.st;
+  pdl_wait();
+  pdl_launch_dependents();
+  if (a.reset_queue && blockIdx.x == 0 && threadIdx.x == 0) *a.reset_queue = 0;
+  for (int bt = blockIdx.x * blockDim.x + threadIdx.x; bt < a.n_seeds; bt += gridDim.x * blockDim.x) {
+    int n, vo, b;
+    if (a.seed_tab) {
+      const int4 e = a.seed_tab[bt];
+      n = e.x;
+      vo = e.y;
+      b = e.z;
+    } else {
+      n = a.horizon * D;
+      vo = bt * n;
+      b = bt;
+    }
+    float* x = st.x + vo;
+    float* g = st.g + vo;
+    float xr[N], gr[N];
+    lane_load(xr, x, n);
+    lane_load(gr, g, n);
+
+    // ---------------- line-search selection (Alg. 1) ----------------
+    if (a.do_select) {
+      float dr[N];
+      lane_load(dr, st.dir + vo, n);
+      const float* cand = st.cand + (long long)vo * na;
+      const float* cgrad = st.cand_grad + (long long)vo * na;
+      const float c0 = st.c[b];
+      const float gd0 = lane_dot(gr, dr, n);
+      int idx = 0;
+      float cnew = st.cand_cost[b * na];
+      for (int l = 0; l < na; ++l) {
+        const float cl = st.cand_cost[b * na + l];
+        bool ok = cl <= c0 + a.prm.armijo_c1 * a.prm.alpha[l] * gd0;
+        if (a.prm.flags & CR_WOLFE) {
+          float gl[N];
+          lane_load(gl, cgrad + (long long)l * n, n);
+          const float gld = lane_dot(gl, dr, n);
+          if (a.prm.flags & CR_STRONG_WOLFE)
+            ok = ok && fabsf(gld) <= a.prm.wolfe_c2 * fabsf(gd0);
+          else
+            ok = ok && gld >= a.prm.wolfe_c2 * gd0;
+        }
+        if (ok) {  // largest passing index; 0 when none passes
+          idx = l;
+          cnew = cl;
+        }
+      }
+      const bool better = cnew < st.best_c[b];  // NaN never improves the best
+      lane_load(xr, cand + (long long)idx * n, n);
+      lane_load(gr, cgrad + (long long)idx * n, n);
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        if (k < n) {
+          x[k] = xr[k];
+          g[k] = gr[k];
+          if (better) st.best_x[vo + k] = xr[k];
+        }
+      }
+      st.c[b] = cnew;
+      st.ls_index[b] = idx;
+      if (better) {
+        st.best_c[b] = cnew;
+        st.best_cfree[b] = st.cand_cfree[b * na + idx];
+      }
+    }
+    if (a.init_best) {
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        if (k < n) st.best_x[vo + k] = xr[k];
+      st.best_c[b] = st.c[b];
+    }
+
+    // ---------------- L-BFGS step (App. A.7) ----------------
+    if (a.do_propose) {
+      float* s_g = st.s + (long long)vo * m;
+      float* y_g = st.y + (long long)vo * m;
+      float* rho_g = st.rho + b * m;
+      const int it = st.iter[b];
+      int shift = 0;
+      if (it > 0) {
+        const int w = (it - 1) % m;
+        float sv[N], yv[N], xp[N], gp[N];
+        lane_load(xp, st.x_prev + vo, n);
+        lane_load(gp, st.g_prev + vo, n);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          sv[k] = k < n ? xr[k] - xp[k] : 0.f;
+          yv[k] = k < n ? gr[k] - gp[k] : 0.f;
+          if (k < n) {
+            s_g[(long long)w * n + k] = sv[k];
+            y_g[(long long)w * n + k] = yv[k];
+          }
+        }
+        const float ys = lane_dot(yv, sv, n);
+        rho_g[w] = ys > 1e-8f ? 1.f / ys : 0.f;
+        shift = it % m;
+      }
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        if (k < n) {
+          st.x_prev[vo + k] = xr[k];
+          st.g_prev[vo + k] = gr[k];
+        }
+      }
+      st.iter[b] = it + 1;
+
+      // two-loop recursion: q = g; newest to oldest
+      float q[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) q[k] = gr[k];
+      float alpha[CR_MAX_HISTORY];
+      for (int i = m - 1; i >= 0; --i) {
+        const int p = (i + shift) % m;
+        const float rho = rho_g[p];
+        if (rho == 0.f) {  // inert pair: alpha = 0, q unchanged
+          alpha[i] = 0.f;
+          continue;
+        }
+        float sp[N], yp[N];
+        lane_load(sp, s_g + (long long)p * n, n);
+        lane_load(yp, y_g + (long long)p * n, n);
+        const float al = rho * lane_dot(sp, q, n);
+        alpha[i] = al;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          if (k < n) q[k] = fmaf(-al, yp[k], q[k]);
+      }
+      // H0 = gamma I from the newest valid pair
+      float gamma = 1.f;
+      for (int i = m - 1; i >= 0; --i) {
+        const int p = (i + shift) % m;
+        if (rho_g[p] > 0.f) {
+          float sp[N], yp[N];
+          lane_load(sp, s_g + (long long)p * n, n);
+          lane_load(yp, y_g + (long long)p * n, n);
+          gamma = lane_dot(sp, yp, n) / lane_dot(yp, yp, n);
+          break;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < N; ++k) q[k] *= gamma;
+      for (int i = 0; i < m; ++i) {
+        const int p = (i + shift) % m;
+        const float rho = rho_g[p];
+        if (rho == 0.f) continue;
+        float sp[N], yp[N];
+        lane_load(sp, s_g + (long long)p * n, n);
+        lane_load(yp, y_g + (long long)p * n, n);
+        const float coef = alpha[i] - rho * lane_dot(yp, q, n);
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          if (k < n) q[k] = fmaf(sp[k], coef, q[k]);
+      }
+      // direction and the clipped candidates of Alg. 1
+      float* dir = st.dir + vo;
+      float* cand = st.cand + (long long)vo * na;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        if (k < n) {
+          const float dk = -q[k];
+          dir[k] = dk;
+          const float lo = a.q_lo[k % D], hi = a.q_hi[k % D];
+          for (int l = 0; l < na; ++l) {
+            float v = fmaf(a.prm.alpha[l], dk, xr[k]);
+            v = fminf(fmaxf(v, lo), hi);
+            cand[(long long)l * n + k] = v;
+          }
+        }
+      }
+    }
+  }
+}
+
 // The largest dynamic shared memory any launch may ask for is set once per
 // kernel and device (never lowered), so launches captured in a graph stay
 // valid whatever is launched later.
@@ -461,7 +668,12 @@ cudaError_t launch_opt(const OptArgs& a, int n_max, cudaStream_t stream) {
   if (a.n_seeds <= 0) return cudaSuccess;
   if (n_max > kMaxN) return cudaErrorInvalidValue;
   const int smem = a.do_propose ? opt_smem_bytes(a.prm.history, n_max) : 0;
-  if (n_max <= 32) return launch_opt_as<32, 1>(a, smem, stream);
+  if (n_max <= 32) {
+    const int grid = (a.n_seeds + 127) / 128;
+    if (n_max <= 8) return launch_pdl(k_opt_lane<8>, grid, 128, 0, stream, a);
+    if (n_max <= 16) return launch_pdl(k_opt_lane<16>, grid, 128, 0, stream, a);
+    return launch_pdl(k_opt_lane<32>, grid, 128, 0, stream, a);
+  }
   if (n_max <= 64) return launch_opt_as<32, 2>(a, smem, stream);
   if (n_max <= 128) return launch_opt_as<32, 4>(a, smem, stream);
   if (n_max <= kVirt) return launch_opt_as<32, 8>(a, smem, stream);

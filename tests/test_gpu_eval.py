@@ -171,6 +171,45 @@ def test_eval_parity_ik():
     assert gpu["cfree"].any() and not gpu["cfree"].all()
 
 
+@pytest.mark.parametrize("spheres, horizon", [(synth.SPHERES_60, 3), ((12, 12, 12, 12, 12, 12, 12), 1)])
+def test_eval_parity_ik_paths(spheres, horizon):
+    """IK mode on the per-trajectory kernel: several independent states per
+    trajectory (costs summed, pose goal at the last one), and a robot of 84
+    spheres (more than the pair table covers: every listed pair of a close
+    link pair is visited); 70 boxes (two chunks of the link box masks)."""
+    rb, w, _ = scene(spheres=spheres, n_boxes=70, world_seed=11)
+    rng = np.random.default_rng(12)
+    goal = f32(oracle.goal_pose_from_fk(rb, synth.uniform_config(rng, rb)))
+    theta = f32(synth.uniform_config(rng, rb, 37 * horizon).reshape(37, horizon, rb.dof))
+    pr = synth.Problem(world=w, q_start=f32(synth.uniform_config(rng, rb)), goal=goal, seeds=theta)
+    p = dict(flags=crgb.IK_MODE | crgb.SELF)
+    gpu = _gpu_eval(rb, w, pr, theta, p)
+    ref = oracle.evaluate(rb, w, pr.q_start, pr.goal, theta, p)
+    n_cmp, _ = compare(gpu, ref, label=f"ik paths {len(spheres)} {horizon}")
+    assert n_cmp >= 25
+
+
+def test_eval_parity_ik_self_contact():
+    """IK mode, no boxes: configurations folded onto themselves so that many
+    states have penetrating sphere pairs (the self term's argmax and its
+    gradient, and the collision-free flag from self contact alone)."""
+    rb, w, _ = scene(spheres=synth.SPHERES_60, n_boxes=0)
+    rng = np.random.default_rng(13)
+    lo, hi = np.asarray(rb.q_lo), np.asarray(rb.q_hi)
+    # joints pushed towards their limits fold the chain
+    u = rng.uniform(0.0, 1.0, (300, rb.dof)) ** 0.25 * np.where(rng.uniform(size=(300, rb.dof)) < 0.5, -1, 1)
+    q = f32(0.5 * (lo + hi) + 0.5 * (hi - lo) * u)[:, None, :]
+    goal = f32(oracle.goal_pose_from_fk(rb, synth.uniform_config(rng, rb)))
+    pr = synth.Problem(world=w, q_start=f32(synth.uniform_config(rng, rb)), goal=goal, seeds=q)
+    p = dict(flags=crgb.IK_MODE | crgb.SELF)
+    gpu = _gpu_eval(rb, w, pr, q, p)
+    ref = oracle.evaluate(rb, w, pr.q_start, pr.goal, q, p)
+    n_cmp, _ = compare(gpu, ref, label="ik self contact")
+    assert n_cmp >= 200
+    hit = ref["terms"][:, 1] > 0
+    assert hit.sum() >= 20 and (~hit).sum() >= 20, hit.sum()
+
+
 def test_eval_many_boxes_and_max_horizon():
     """More boxes than one shared-memory chunk (150 > 64) and the largest horizon."""
     rb, w, pr = scene(n_boxes=150, n_seeds=2, horizon=128, world_seed=8, problem_seed=3)

@@ -110,6 +110,33 @@ def test_batched_problems_equal_alone(ctx):
         assert torch.equal(alone.best, t.best)
 
 
+@pytest.mark.parametrize("flags", [0, None])
+def test_small_seeds_equal_wide_kernel(ctx, flags):
+    """Seeds of at most 32 variables run one per thread; alone they must give
+    bit for bit what the block-wide optimiser gives them inside a batch with a
+    long-horizon problem (every dot product in the same order).  Trajectory
+    mode with H = 4 (28 variables) and IK mode (7 variables, plus H = 48
+    states evaluated as independent states in the same batch)."""
+    rb = scene(spheres=synth.SPHERES_60)[0]
+    R = crgb.Robot(rb)
+    params = None if flags is None else dict(flags=crgb.IK_MODE | crgb.SELF | crgb.WOLFE)
+    small_h = 4 if flags is None else 1
+    specs = []
+    for k, (K, B, H) in enumerate([(6, 8, small_h), (12, 4, 48)]):
+        _, w, pr = scene(spheres=synth.SPHERES_60, n_boxes=K, n_seeds=B, horizon=H, world_seed=30 + k,
+                         problem_seed=40 + k)
+        specs.append(_spec(crgb.World(w), pr))
+    together = crgb.solve(ctx, R, specs, params, iters=6, graph=True, persistent=True)
+    torch.cuda.synchronize()
+    alone = crgb.solve(ctx, R, [specs[0]], params, iters=6, graph=False, persistent=False)[0]
+    torch.cuda.synchronize()
+    t = together[0]
+    assert torch.equal(alone.traj, t.traj)
+    assert torch.equal(alone.cost, t.cost)
+    assert torch.equal(alone.cfree, t.cfree)
+    assert torch.equal(alone.best, t.best)
+
+
 def test_solve_result_is_consistent_with_oracle(ctx):
     """Returned best iterates: their oracle cost matches the reported cost
     (1e-4 rel, unless near a decision threshold) and the reported best index
