@@ -25,9 +25,19 @@ namespace {
 
 constexpr int kIkThreads = 128;  // threads of a CTA (4 warps)
 constexpr int kNear = 8;         // near spheres of one link kept in registers by the self term
+constexpr int kIkSplit = 8;      // threads per trajectory in small launches
+constexpr long long kIkSplitBelow = 16384;  // trajectories below which a launch is small
 
-template <int NT>
+// TPT threads share a trajectory (consecutive lanes): thread `sub` takes the
+// links l with l % TPT == sub for the world term and the link pairs g with
+// g % TPT == sub for the self term; the partial results are combined in link
+// order (costs, gradients) or by an order-free rule (the deepest pair, the
+// collision-free flag), so every TPT gives the same bits.  Large launches use
+// TPT = 1 (throughput), small ones TPT = 8 (latency).
+template <int NT, int TPT>
 __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs a) {
+  static_assert(TPT == 1 || TPT == 2 || TPT == 4 || TPT == 8 || TPT == 16, "TPT");
+  constexpr int kOwn = (kMaxDof + TPT - 1) / TPT;  // links a thread can own
   // rows of this thread's link transforms, s_tf[(l * 3 + row) * NT + tid],
   // then its link bounding-sphere centres, s_lc[l * NT + tid] (w: radius)
   extern __shared__ float4 s_tf[];
@@ -53,6 +63,8 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
   // the pair table (robots of up to 64 spheres) lets the self term visit only
   // the pairs of spheres that are near the other link
   const int16_t* pair_at = a.rb.pair_at;
+  const int sub = TPT == 1 ? 0 : tid % TPT;
+  const unsigned gmask = TPT == 1 ? 0xffffffffu : ((1u << TPT) - 1u) << ((tid & 31) & ~(TPT - 1));
 
   auto row = [&](int l, int r) -> float4 { return s_tf[(l * 3 + r) * NT + tid]; };
   // world position of a point with link-frame centre c on link l
@@ -65,9 +77,11 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
 
   const int per_tile = a.problems ? a.max_traj : a.traj_per_tile;
   const int n_tiles = a.problems ? a.n_tiles : (a.prob0.n_traj + a.traj_per_tile - 1) / a.traj_per_tile;
-  const long long n_slots = (long long)n_tiles * per_tile;
-  for (long long gs = (long long)blockIdx.x * NT + tid; gs < n_slots; gs += (long long)gridDim.x * NT) {
-    const int tile = (int)(gs / per_tile), r = (int)(gs % per_tile);
+  const long long n_threads = (long long)n_tiles * per_tile * TPT;
+  // the TPT threads of a trajectory always take the same trip through this loop
+  for (long long gs = (long long)blockIdx.x * NT + tid; gs < n_threads; gs += (long long)gridDim.x * NT) {
+    const long long slot = gs / TPT;
+    const int tile = (int)(slot / per_tile), r = (int)(slot % per_tile);
     const ProblemView* pv;
     int r0, nt;
     if (a.problems) {
@@ -92,7 +106,8 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
       float q[kMaxDof];
 #pragma unroll
       for (int j = 0; j < kMaxDof; ++j) q[j] = j < D ? th[j] : 0.f;
-      // ---- forward kinematics (Sec. 3.1) into this thread's rows
+      // ---- forward kinematics (Sec. 3.1) into this thread's rows (every
+      // thread of the trajectory keeps its own copy)
       {
         float T[12] = {1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f};
 #pragma unroll
@@ -114,39 +129,51 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
           s_lc[l * NT + tid] = make_float4(c.x, c.y, c.z, lb.w);
         }
       }
-      // joint gradient of this state (App. E.1 joint table: revolute joint j
-      // moves a point x by a_j x (x - o_j))
+      // joint j's share of a force gx on point x of a link at or after j
+      // (App. E.1 joint table: revolute joint j moves x by a_j x (x - o_j))
+      auto joint_share = [&](int j, V3 x, V3 gx) -> float {
+        const float4 r0 = row(j, 0), r1 = row(j, 1), r2 = row(j, 2);
+        const int ax = s_axis[j];
+        const V3 aj = ax == 0 ? v3(r0.x, r1.x, r2.x) : ax == 1 ? v3(r0.y, r1.y, r2.y) : v3(r0.z, r1.z, r2.z);
+        return dot(gx, cross(aj, x - v3(r0.w, r1.w, r2.w)));
+      };
+      // the state's joint gradient, kept by the thread with sub == 0
       float g[kMaxDof];
 #pragma unroll
       for (int j = 0; j < kMaxDof; ++j) g[j] = 0.f;
-      // a force gx on point x of link l: joint j <= l gets gx . (a_j x (x - o_j))
-      auto to_joints = [&](int l, V3 x, V3 gx) {
-#pragma unroll
-        for (int j = 0; j < kMaxDof; ++j) {
-          if (j > l) break;
-          const float4 r0 = row(j, 0), r1 = row(j, 1), r2 = row(j, 2);
-          const int ax = s_axis[j];
-          const V3 aj = ax == 0 ? v3(r0.x, r1.x, r2.x) : ax == 1 ? v3(r0.y, r1.y, r2.y) : v3(r0.z, r1.z, r2.z);
-          g[j] += dot(gx, cross(aj, x - v3(r0.w, r1.w, r2.w)));
-        }
-      };
+      float tws = 0.f;  // the state's world cost
 
-      // ---- world term (Eq. 10-11, discrete): per link, the boxes whose
-      // bounding sphere is within reach of the link's bounding sphere, in
-      // chunks of 64; then each sphere of the link against those boxes
+      // ---- world term (Eq. 10-11, discrete), link by link: the boxes whose
+      // bounding sphere is within reach of the link's bounding sphere (64 at
+      // a time), then each sphere of the link against those boxes.  Link l
+      // gives a cost c_l and a gradient G_l (joints j <= l), both summed over
+      // its spheres in order; the state's sums run over l in order.
+      float c_own[kOwn], G_own[kOwn][kMaxDof];
+#pragma unroll
+      for (int k = 0; k < kOwn; ++k) {
+        c_own[k] = 0.f;
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j) G_own[k][j] = 0.f;
+      }
       if (K > 0) {
-        for (int l = 0; l < D; ++l) {
+#pragma unroll
+        for (int k = 0; k < kOwn; ++k) {
+          const int l = sub + k * TPT;
+          if (l >= D) break;
           const float4 lc = s_lc[l * NT + tid];
           if (lc.w < 0.f) continue;  // no enabled sphere
-          const V3 cl = v3(lc.x, lc.y, lc.z);
           const float reach = lc.w + eta;
           const int s0 = __ldg(&a.rb.link_start[l]), s1 = __ldg(&a.rb.link_start[l + 1]);
+          float cl = 0.f;
+          float Gl[kMaxDof];
+#pragma unroll
+          for (int j = 0; j < kMaxDof; ++j) Gl[j] = 0.f;
           for (int c0 = 0; c0 < K; c0 += 64) {
             const int kc = min(64, K - c0);
             unsigned long long m = 0ull;
             for (int kk = 0; kk < kc; ++kk) {
               const float4 bc = __ldg(&boxes[c0 + kk].c);
-              const float dx = cl.x - bc.x, dy = cl.y - bc.y, dz = cl.z - bc.z;
+              const float dx = lc.x - bc.x, dy = lc.y - bc.y, dz = lc.z - bc.z;
               const float rb = (reach + bc.w) * 1.0001f + 1e-6f;
               if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rb * rb) m |= 1ull << kk;
             }
@@ -181,13 +208,41 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
                 }
               }
               if (S != 0.f || gs3.x != 0.f || gs3.y != 0.f || gs3.z != 0.f) {
-                tw += prm.w_coll * S;
-                to_joints(l, x, prm.w_coll * gs3);
+                cl += prm.w_coll * S;
+                const V3 gx = prm.w_coll * gs3;
+#pragma unroll
+                for (int j = 0; j < kMaxDof; ++j) {
+                  if (j > l) break;
+                  Gl[j] += joint_share(j, x, gx);
+                }
               }
             }
           }
+          if (TPT == 1) {  // links come in order: add at once
+            tws += cl;
+#pragma unroll
+            for (int j = 0; j < kMaxDof; ++j) g[j] += Gl[j];
+          } else {
+            c_own[k] = cl;
+#pragma unroll
+            for (int j = 0; j < kMaxDof; ++j) G_own[k][j] = Gl[j];
+          }
         }
       }
+      if (TPT > 1) {
+        // link l's sums from thread l % TPT, in link order
+#pragma unroll
+        for (int l = 0; l < kMaxDof; ++l) {
+          if (l >= D) break;
+          tws += __shfl_sync(gmask, c_own[l / TPT], l % TPT, TPT);
+#pragma unroll
+          for (int j = 0; j < kMaxDof; ++j) {
+            if (j > l) break;
+            g[j] += __shfl_sync(gmask, G_own[l / TPT][j], l % TPT, TPT);
+          }
+        }
+      }
+      tw += tws;
 
       // ---- self term (Eq. 9): link pairs whose bounding spheres are within
       // 1 mm; with the pair table, only the pairs whose two spheres are each
@@ -198,6 +253,14 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
       if (P > 0) {
         float best = 0.f;
         int arg = -1;
+        auto take = [&](float pen, int p) {
+          if (pen > best) {
+            best = pen;
+            arg = p;
+          } else if (pen == best && pen > 0.f && __ldg(&a.rb.pair_orig[p]) < __ldg(&a.rb.pair_orig[arg])) {
+            arg = p;
+          }
+        };
         auto test_pair = [&](int p, int i, int j) {
           const float4 ci = __ldg(&a.rb.spheres[i]), cj = __ldg(&a.rb.spheres[j]);
           if (ci.w <= 0.f || cj.w <= 0.f) return;
@@ -207,14 +270,9 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
           if (d2 >= lp * lp) return;  // more than 1 mm apart
           const float pen = rs - sqrtf(d2);
           if (!(-pen > 0.f)) free_ok = false;
-          if (pen > best) {
-            best = pen;
-            arg = p;
-          } else if (pen == best && pen > 0.f && __ldg(&a.rb.pair_orig[p]) < __ldg(&a.rb.pair_orig[arg])) {
-            arg = p;
-          }
+          take(pen, p);
         };
-        for (int gi = 0; gi < G; ++gi) {
+        for (int gi = sub; gi < G; gi += TPT) {
           const int4 gr = __ldg(&a.rb.groups[gi]);
           const float4 la = s_lc[gr.x * NT + tid], lbb = s_lc[gr.y * NT + tid];
           if (la.w < 0.f || lbb.w < 0.f) continue;
@@ -237,9 +295,9 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
                 const float x = fmaf(r0.x, c.x, fmaf(r0.y, c.y, fmaf(r0.z, c.z, r0.w)));
                 const float y = fmaf(r1.x, c.x, fmaf(r1.y, c.y, fmaf(r1.z, c.z, r1.w)));
                 const float z = fmaf(r2.x, c.x, fmaf(r2.y, c.y, fmaf(r2.z, c.z, r2.w)));
-                const float dx = x - la.x, dy = y - la.y, dz = z - la.z;
+                const float ex = x - la.x, ey = y - la.y, ez = z - la.z;
                 const float li = c.w + la.w + 1e-3f;
-                if (!(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < li * li)) continue;
+                if (!(fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < li * li)) continue;
                 const int j = __ldg(&a.rb.link_sph[qq]);
 #pragma unroll
                 for (int k = 0; k < kNear; ++k)
@@ -277,13 +335,7 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
                   if (p < 0) continue;  // not a listed pair
                   const float pen = rs - sqrtf(d2);
                   if (!(-pen > 0.f)) free_ok = false;
-                  if (pen > best) {
-                    best = pen;
-                    arg = p;
-                  } else if (pen == best && pen > 0.f &&
-                             __ldg(&a.rb.pair_orig[p]) < __ldg(&a.rb.pair_orig[arg])) {
-                    arg = p;
-                  }
+                  take(pen, p);
                 }
               }
             }
@@ -295,9 +347,21 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
             }
           }
         }
+        if (TPT > 1) {  // the deepest pair over the trajectory's threads (order-free)
+#pragma unroll
+          for (int o = TPT / 2; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(gmask, best, o, TPT);
+            const int oa = __shfl_xor_sync(gmask, arg, o, TPT);
+            if (ob > best || (ob == best && ob > 0.f && oa != arg &&
+                              __ldg(&a.rb.pair_orig[oa]) < __ldg(&a.rb.pair_orig[arg]))) {
+              best = ob;
+              arg = oa;
+            }
+          }
+        }
         if (selfc) {
           ts += prm.w_self * best;
-          if (arg >= 0) {
+          if (arg >= 0 && sub == 0) {
             const uint32_t pr = __ldg(&a.rb.pairs[arg]);
             const int pi = (int)(pr & 0xffffu), pj = (int)(pr >> 16);
             const int li = __ldg(&a.rb.sphere_link[pi]), lj = __ldg(&a.rb.sphere_link[pj]);
@@ -306,12 +370,22 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
             const float n = norm(d);
             if (n > 0.f) {
               const float f = prm.w_self / n;
-              to_joints(li, xi, (-f) * d);
-              to_joints(lj, xj, f * d);
+#pragma unroll
+              for (int j = 0; j < kMaxDof; ++j) {
+                if (j > li) break;
+                g[j] += joint_share(j, xi, (-f) * d);
+              }
+#pragma unroll
+              for (int j = 0; j < kMaxDof; ++j) {
+                if (j > lj) break;
+                g[j] += joint_share(j, xj, f * d);
+              }
             }
           }
         }
       }
+      if (TPT > 1) free_ok = __all_sync(gmask, free_ok);
+      if (sub != 0) continue;  // the rest of the state: one thread
 
       // ---- Eq. 14 pose goal and Eq. 15 joint-space goal at the last state
       if (t == H - 1) {
@@ -393,6 +467,7 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
       }
     }
 
+    if (sub != 0) continue;
     const int gi = pv->traj_base + r0 + r;
     a.cost[gi] = tw + ts + tb + tg;
     if (a.cfree) a.cfree[gi] = (uint8_t)free_ok;
@@ -419,8 +494,11 @@ static cudaError_t allow_ik_smem() {
   cudaGetDevice(&dev);
   const unsigned bit = 1u << (dev & 31);
   if (done & bit) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_eval_ik<kIkThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_eval_ik<kIkThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        eval_ik_smem_bytes(kMaxDof));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_eval_ik<kIkThreads, kIkSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             eval_ik_smem_bytes(kMaxDof));
   if (e == cudaSuccess) done |= bit;
   return e;
 }
@@ -428,7 +506,7 @@ static cudaError_t allow_ik_smem() {
 int eval_ik_blocks_per_sm(int dof) {
   int n = 0;
   if (allow_ik_smem() != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval_ik<kIkThreads>, kIkThreads,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval_ik<kIkThreads, 1>, kIkThreads,
                                                     eval_ik_smem_bytes(dof)) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
@@ -442,9 +520,12 @@ cudaError_t launch_eval_ik(const EvalArgs& a, cudaStream_t stream) {
   const int smem = eval_ik_smem_bytes(a.rb.dof);
   cudaError_t e = allow_ik_smem();
   if (e != cudaSuccess) return e;
-  const long long want = (n_slots + kIkThreads - 1) / kIkThreads;
+  // few trajectories: several threads each, for latency (same results)
+  const bool split = n_slots < kIkSplitBelow;
+  const long long want = (n_slots * (split ? kIkSplit : 1) + kIkThreads - 1) / kIkThreads;
   const int grid = (int)(want < (1ll << 30) ? want : (1ll << 30));
-  return launch_pdl(k_eval_ik<kIkThreads>, grid, kIkThreads, (size_t)smem, stream, a);
+  return split ? launch_pdl(k_eval_ik<kIkThreads, kIkSplit>, grid, kIkThreads, (size_t)smem, stream, a)
+               : launch_pdl(k_eval_ik<kIkThreads, 1>, grid, kIkThreads, (size_t)smem, stream, a);
 }
 
 }  // namespace crgb

@@ -25,6 +25,7 @@ namespace {
 constexpr int kVirt = 256;        // virtual threads per seed
 constexpr int kSlots = 8;         // most element slots per physical thread
 constexpr int kMaxN = kVirt * kSlots;
+constexpr int kLaneSeedsFrom = 4096;  // seeds of <= 32 variables: one thread each from this many
 
 // Partial sums of one dot product for NT physical threads holding SLOTS
 // element slots each (element k = tid + NT * e).  With NT = 256 every slot of
@@ -668,12 +669,15 @@ cudaError_t launch_opt(const OptArgs& a, int n_max, cudaStream_t stream) {
   if (a.n_seeds <= 0) return cudaSuccess;
   if (n_max > kMaxN) return cudaErrorInvalidValue;
   const int smem = a.do_propose ? opt_smem_bytes(a.prm.history, n_max) : 0;
-  if (n_max <= 32) {
+  // many seeds of at most 32 variables: one thread per seed (throughput);
+  // few: one warp per seed (latency); both give the same bits
+  if (n_max <= 32 && a.n_seeds >= kLaneSeedsFrom) {
     const int grid = (a.n_seeds + 127) / 128;
     if (n_max <= 8) return launch_pdl(k_opt_lane<8>, grid, 128, 0, stream, a);
     if (n_max <= 16) return launch_pdl(k_opt_lane<16>, grid, 128, 0, stream, a);
     return launch_pdl(k_opt_lane<32>, grid, 128, 0, stream, a);
   }
+  if (n_max <= 32) return launch_opt_as<32, 1>(a, smem, stream);
   if (n_max <= 64) return launch_opt_as<32, 2>(a, smem, stream);
   if (n_max <= 128) return launch_opt_as<32, 4>(a, smem, stream);
   if (n_max <= kVirt) return launch_opt_as<32, 8>(a, smem, stream);

@@ -189,6 +189,24 @@ def test_eval_parity_ik_paths(spheres, horizon):
     assert n_cmp >= 25
 
 
+def test_eval_ik_small_and_large_launches_agree():
+    """IK mode: a small launch runs several threads per trajectory, a large
+    one a thread each; the same trajectories give the same bits either way."""
+    rb, w, _ = scene(spheres=synth.SPHERES_60, n_boxes=40, world_seed=21)
+    R, W = crgb.Robot(rb), crgb.World(w)
+    rng = np.random.default_rng(22)
+    goal = f32(oracle.goal_pose_from_fk(rb, synth.uniform_config(rng, rb)))
+    q = torch.tensor(synth.uniform_config(rng, rb, 20000)[:, None, :], dtype=torch.float32, device="cuda")
+    spec = crgb.ProblemSpec(W, f32(synth.uniform_config(rng, rb)), goal, 1)
+    p = dict(flags=crgb.IK_MODE | crgb.SELF)
+    small = crgb.evaluate(R, spec, q[:100].contiguous(), p)
+    large = crgb.evaluate(R, spec, q, p)
+    torch.cuda.synchronize()
+    for k in ("cost", "grad", "cfree", "terms"):
+        assert torch.equal(small[k], large[k][:100]), k
+    assert 0 < int(large["cfree"].sum()) < 20000
+
+
 def test_eval_parity_ik_self_contact():
     """IK mode, no boxes: configurations folded onto themselves so that many
     states have penetrating sphere pairs (the self term's argmax and its

@@ -137,6 +137,29 @@ def test_small_seeds_equal_wide_kernel(ctx, flags):
     assert torch.equal(alone.best, t.best)
 
 
+def test_ik_small_and_large_batches_agree(ctx):
+    """IK solves: alone, a problem of 8 seeds runs the one-warp optimiser and
+    the split evaluation; inside a batch of 4104 seeds the per-thread
+    optimiser and the one-thread evaluation.  Same bits."""
+    rb = scene(spheres=synth.SPHERES_60)[0]
+    R = crgb.Robot(rb)
+    params = dict(flags=crgb.IK_MODE | crgb.SELF | crgb.WOLFE)
+    specs = []
+    for k, B in enumerate((8, 4096)):
+        _, w, pr = scene(spheres=synth.SPHERES_60, n_boxes=20, n_seeds=B, horizon=1, world_seed=50 + k,
+                         problem_seed=60 + k)
+        specs.append(_spec(crgb.World(w), pr))
+    together = crgb.solve(ctx, R, specs, params, iters=8, graph=True, persistent=True)
+    torch.cuda.synchronize()
+    alone = crgb.solve(ctx, R, [specs[0]], params, iters=8, graph=False, persistent=False)[0]
+    torch.cuda.synchronize()
+    t = together[0]
+    assert torch.equal(alone.traj, t.traj)
+    assert torch.equal(alone.cost, t.cost)
+    assert torch.equal(alone.cfree, t.cfree)
+    assert torch.equal(alone.best, t.best)
+
+
 def test_solve_result_is_consistent_with_oracle(ctx):
     """Returned best iterates: their oracle cost matches the reported cost
     (1e-4 rel, unless near a decision threshold) and the reported best index
