@@ -112,6 +112,12 @@ def lib():
                                         _dp, _dp, _dp]
         L.cro_retime.argtypes = [C.POINTER(_Robot), C.c_int32, _dp, _dp]
         L.cro_retime.restype = C.c_double
+        L.cro_pose_error.argtypes = [C.POINTER(_Robot), _dp, _dp]
+        L.cro_pose_error.restype = C.c_double
+        L.cro_rank_seeds.argtypes = [C.POINTER(_Robot), C.c_int32, C.c_int32, _dp, _dp, _dp,
+                                     C.POINTER(C.c_uint8), _dp, C.c_double, C.c_int32, C.c_double,
+                                     C.c_double, C.c_double, C.c_double, _dp]
+        L.cro_rank_seeds.restype = C.c_int32
         L.cro_steer_steps.argtypes = [C.c_int32, C.c_int32, _dp, C.c_double]
         L.cro_steer_steps.restype = C.c_int32
         L.cro_steer.argtypes = [C.POINTER(_Robot), C.POINTER(_World), C.c_int32, _dp, C.c_int32, _ip,
@@ -472,6 +478,31 @@ def steer(rb, world, edges, n):
 # ---------------------------------------------------------------------------
 # App. "Time-step Discretization"
 # ---------------------------------------------------------------------------
+
+def pose_error(rb, q, goal7):
+    """|p - p_g| + d_q of the end effector at configuration q (App. "Solver details")."""
+    keep = _Keep()
+    R = _robot(rb, keep)
+    return float(lib().cro_pose_error(C.byref(R), _p(_f64(q)), _p(_f64(goal7))))
+
+
+def rank_seeds(rb, q0, goal7, theta, cfree, dt=None, dt_all=None, ik=False, w_pose=1.0, w_jerk=1e-3,
+               w_time=1.0, w_dist=0.1):
+    """Scores of seeds theta [B,H,dof] and the index of the lowest-scoring
+    collision-free one (-1 when none), App. "Solver details"."""
+    keep = _Keep()
+    R = _robot(rb, keep)
+    th = _f64(theta)
+    B, H, dof = th.shape
+    score = np.zeros(B)
+    cf = np.ascontiguousarray(np.asarray(cfree, dtype=np.uint8))
+    dtp = None if dt is None else _f64(dt)
+    best = lib().cro_rank_seeds(C.byref(R), H, B, _p(_f64(q0)), _p(_f64(goal7)), _p(th),
+                                cf.ctypes.data_as(C.POINTER(C.c_uint8)), _p(dtp),
+                                float(0.0 if dt_all is None else dt_all), int(bool(ik)), float(w_pose),
+                                float(w_jerk), float(w_time), float(w_dist), _p(score))
+    return score, int(best)
+
 
 def retime(rb, q0, theta):
     """dt that puts one trajectory theta [H, dof] at the robot's limits."""

@@ -955,3 +955,52 @@ double cro_retime(const cro_robot* rb, int32_t H, const double* q0, const double
   free(v); free(a); free(j);
   return dt;
 }
+
+/* ------------------------------------------------------------------------ */
+/* App. "Solver details": choosing among the seeds of a solve                 */
+/* ------------------------------------------------------------------------ */
+
+double cro_pose_error(const cro_robot* rb, const double* q, const double* goal7) {
+  double* lt = (double*)malloc((size_t)rb->dof * 12 * sizeof(double));
+  double* sp = (double*)malloc((size_t)(rb->n_spheres > 0 ? rb->n_spheres : 1) * 4 * sizeof(double));
+  double ee[12], Rg[9];
+  cro_fk(rb, q, lt, sp, ee);
+  free(lt); free(sp);
+  quat_to_rot(goal7 + 3, Rg);
+  double e[3] = {ee[3] - goal7[0], ee[7] - goal7[1], ee[11] - goal7[2]};
+  double tr = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) tr += Rg[a * 3 + b] * ee[a * 4 + b];
+  return norm3(e) + (3.0 - tr) / 4.0;
+}
+
+int32_t cro_rank_seeds(const cro_robot* rb, int32_t H, int32_t B, const double* q0, const double* goal7,
+                       const double* theta, const uint8_t* cfree, const double* dt, double dt_all,
+                       int32_t ik, double w_pose, double w_jerk, double w_time, double w_dist, double* score) {
+  const int D = rb->dof, NS = H + 1;
+  double* v = (double*)malloc((size_t)NS * D * sizeof(double));
+  double* a = (double*)malloc((size_t)NS * D * sizeof(double));
+  double* j = (double*)malloc((size_t)NS * D * sizeof(double));
+  int32_t best = -1;
+  for (int b = 0; b < B; ++b) {
+    const double* th = theta + (size_t)b * H * D;
+    const double* last = th + (size_t)(H - 1) * D;
+    double s = w_pose * cro_pose_error(rb, last, goal7);
+    if (ik) {
+      double d2 = 0.0;
+      for (int k = 0; k < D; ++k) d2 += (last[k] - q0[k]) * (last[k] - q0[k]);
+      s += w_dist * sqrt(d2);
+    } else {
+      const double dtb = dt ? dt[b] : dt_all;
+      cro_stencil(H, D, q0, th, dtb, v, a, j);
+      double jmax = 0.0;
+      for (int k = 0; k < NS * D; ++k)
+        if (fabs(j[k]) > jmax) jmax = fabs(j[k]);
+      s += w_jerk * jmax + w_time * H * dtb;
+    }
+    score[b] = s;
+    if (cfree[b] && !isnan(s) && (best < 0 || s < score[best])) best = b;
+  }
+  free(v); free(a); free(j);
+  return best;
+}

@@ -229,6 +229,25 @@ void cro_steer(const cro_robot* rb, const cro_world* w, int32_t E, const double*
  * theta [H][dof] (one trajectory), q0 the start configuration. */
 double cro_retime(const cro_robot* rb, int32_t H, const double* q0, const double* theta);
 
+/* ------------------------------------------------------------------------ */
+/* App. "Solver details": choosing among the seeds of a solve                 */
+/* ------------------------------------------------------------------------ */
+
+/* Pose error of a configuration's end effector against goal7 (xyz + quat
+ * wxyz): |p - p_g| + d_q with d_q = (3 - tr(R_g^T R)) / 4 of Eq. 14. */
+double cro_pose_error(const cro_robot* rb, const double* q, const double* goal7);
+
+/* Score of each of B seeds (theta [B][H][dof], start q0):
+ *   ik != 0:  w_pose * e_pose(theta_H) + w_dist * |theta_H - q0|
+ *   ik == 0:  w_pose * e_pose(theta_H) + w_jerk * max |jerk| + w_time * H * dt_b
+ * with the jerk of App. A.5's five-point stencil at dt_b (dt[b], or dt_all
+ * when dt is NULL) over every sample and joint.  Returns the index of the
+ * lowest score among seeds with cfree[b] != 0 (the lowest index on ties; a
+ * NaN score never wins), or -1 when there is none. */
+int32_t cro_rank_seeds(const cro_robot* rb, int32_t H, int32_t B, const double* q0, const double* goal7,
+                       const double* theta, const uint8_t* cfree, const double* dt, double dt_all,
+                       int32_t ik, double w_pose, double w_jerk, double w_time, double w_dist, double* score);
+
 #ifdef __cplusplus
 }
 #endif

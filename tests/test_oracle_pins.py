@@ -943,3 +943,86 @@ def test_retime_scaling_and_limits(oracle_mod):
     assert dt2 / dt == pytest.approx(2.0) or dt2 / dt == pytest.approx(np.sqrt(2.0)) or \
         dt2 / dt == pytest.approx(np.cbrt(2.0))
     assert oracle_mod.retime(rb, q0, np.tile(q0, (H, 1))) < 1e-6   # rounding residue only (cube root)
+
+
+def _axis_angle(axis, phi):
+    """Rotation matrix about a unit axis (Rodrigues), for the pose-error pins."""
+    k = np.asarray(axis, dtype=np.float64)
+    k = k / np.linalg.norm(k)
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + math.sin(phi) * K + (1 - math.cos(phi)) * K @ K
+
+
+def _quat(R):
+    """wxyz of a rotation matrix (Shepperd's method, trace branch + fallbacks)."""
+    tr = np.trace(R)
+    if tr > 0:
+        s = math.sqrt(tr + 1.0) * 2
+        q = [0.25 * s, (R[2, 1] - R[1, 2]) / s, (R[0, 2] - R[2, 0]) / s, (R[1, 0] - R[0, 1]) / s]
+    else:
+        i = int(np.argmax(np.diag(R)))
+        j, k = (i + 1) % 3, (i + 2) % 3
+        s = math.sqrt(1.0 + R[i, i] - R[j, j] - R[k, k]) * 2
+        q = [0.0] * 4
+        q[0] = (R[k, j] - R[j, k]) / s
+        q[1 + i] = 0.25 * s
+        q[1 + j] = (R[j, i] + R[i, j]) / s
+        q[1 + k] = (R[k, i] + R[i, k]) / s
+    q = np.asarray(q)
+    return q / np.linalg.norm(q)
+
+
+def test_pose_error_closed_forms(oracle_mod):
+    """App. "Solver details" pose error |p - p_g| + d_q: a goal displaced by a
+    vector delta with the same orientation gives |delta|; a goal rotated by
+    phi about any axis through the end effector gives (1 - cos phi) / 2."""
+    rb = synth.make_robot(synth.SPHERES_42, seed=0)
+    rng = np.random.default_rng(40)
+    q = synth.uniform_config(rng, rb)
+    _, _, ee = oracle_mod.fk(rb, q)
+    E = np.asarray(ee).reshape(3, 4)
+    p, R = E[:, 3], E[:, :3]
+    delta = np.array([0.03, -0.04, 0.12])
+    assert oracle_mod.pose_error(rb, q, np.concatenate([p + delta, _quat(R)])) == \
+        pytest.approx(np.linalg.norm(delta), abs=1e-12)
+    for phi in (0.1, 1.0, 2.5):
+        Rg = R @ _axis_angle(rng.normal(size=3), phi)
+        assert oracle_mod.pose_error(rb, q, np.concatenate([p, _quat(Rg)])) == \
+            pytest.approx((1 - math.cos(phi)) / 2, abs=1e-12)
+
+
+def test_rank_seeds_closed_forms_and_choice(oracle_mod):
+    """Seed scores of App. "Solver details": at rest on the goal only the motion
+    time H dt remains; IK at the goal configuration scores w_dist |q - q0|; the
+    largest jerk equals a direct evaluation of the five-point stencil on the
+    padded sequence; the choice is the lowest collision-free score, the lowest
+    index on ties, never a NaN score, -1 without a collision-free seed."""
+    rb = synth.make_robot(synth.SPHERES_42, seed=0)
+    rng = np.random.default_rng(41)
+    D, H = rb.dof, 16
+    q0 = synth.uniform_config(rng, rb)
+    qg = synth.uniform_config(rng, rb)
+    goal = oracle_mod.goal_pose_from_fk(rb, qg)
+    rest = np.tile(qg, (1, H, 1))
+    s, b = oracle_mod.rank_seeds(rb, qg, goal, rest, [1], dt_all=0.04, w_pose=1.0, w_jerk=1e-3, w_time=2.0)
+    assert s[0] == pytest.approx(2.0 * H * 0.04, abs=1e-9) and b == 0
+    s, _ = oracle_mod.rank_seeds(rb, q0, goal, qg[None, None, :], [1], ik=True, w_pose=1.0, w_dist=0.3)
+    assert s[0] == pytest.approx(0.3 * np.linalg.norm(qg - q0), abs=1e-9)
+    # largest jerk by brute force: ext = [q0 q0 q0 theta_1..theta_H theta_H theta_H]
+    th = q0 + np.cumsum(rng.normal(0, 0.05, size=(3, H, D)), axis=1)
+    dts = np.array([0.03, 0.05, 0.08])
+    s, _ = oracle_mod.rank_seeds(rb, q0, goal, th, [1, 1, 1], dt=dts, w_pose=0.0, w_jerk=1.0, w_time=0.0)
+    for k in range(3):
+        ext = np.concatenate([np.tile(q0, (3, 1)), th[k], np.tile(th[k][-1], (2, 1))])
+        jm = max(abs(-ext[e - 2, j] + 2 * ext[e - 1, j] - 2 * ext[e + 1, j] + ext[e + 2, j]) / (2 * dts[k] ** 3)
+                 for e in range(2, H + 3) for j in range(D))
+        assert s[k] == pytest.approx(jm, rel=1e-12)
+    # choice: seeds 1 and 3 tie and are the lowest collision-free; seed 0 lower but not free;
+    # seed 2 NaN
+    th4 = np.stack([rest[0], rest[0], rest[0], rest[0]])
+    th4[2, -1, 0] = np.nan   # the last state: its pose error is NaN
+    s, b = oracle_mod.rank_seeds(rb, qg, goal, th4, [0, 1, 1, 1], dt=np.array([0.01, 0.02, 0.01, 0.02]),
+                                 w_pose=1.0, w_jerk=0.0, w_time=1.0)
+    assert np.isnan(s[2]) and b == 1
+    _, b = oracle_mod.rank_seeds(rb, qg, goal, th4, [0, 0, 0, 0], dt_all=0.05)
+    assert b == -1
