@@ -272,6 +272,25 @@ cr_status cr_steer(const cr_robot* robot, const cr_world* world, int32_t n_edges
 cr_status cr_retime(const cr_robot* robot, const cr_problem* problem, int32_t B, const float* theta,
                     float* dt, void* stream);
 
+/* Choosing among the seeds of a solve (App. "Solver details": IK returns the
+ * valid solution with the lowest weighted sum of pose error and distance to
+ * the current configuration; trajectory optimisation the valid seed with the
+ * lowest blend of pose error, largest jerk and motion time).  With e_pose =
+ * |p - p_g| + d_q at the last state (d_q = (3 - tr(R_g^T R)) / 4 of Eq. 14):
+ *   params->flags & CR_IK_MODE:  score = w_pose e_pose + w_dist |theta_H - q_start|
+ *   otherwise:                   score = w_pose e_pose + w_jerk max|jerk| + w_time H dt_b
+ * the jerk being App. A.5's five-point stencil at dt_b (dt[b], or params->dt
+ * when dt is NULL) over every sample and joint, H dt_b the motion time of the
+ * H + 1 waypoints.  The paper gives no weights; they are the caller's.
+ *   theta  device [B][H][dof] (H = problem->horizon), cfree device [B] (uint8)
+ *   dt     device [B] per-seed time steps, or NULL
+ *   score  device [B] out; best device [1] out: the lowest score among seeds
+ *          with cfree != 0 (the lowest index on ties; NaN never wins), or -1.
+ * Two launches on `stream`. */
+cr_status cr_rank_seeds(const cr_robot* robot, const cr_problem* problem, const cr_params* params,
+                        int32_t B, const float* theta, const uint8_t* cfree, const float* dt, float w_pose,
+                        float w_jerk, float w_time, float w_dist, float* score, int32_t* best, void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Runtime: context, batched solve                                            */
 /* ------------------------------------------------------------------------- */

@@ -96,6 +96,8 @@ SIGNATURES = {
                           _vp, _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, _vp], C.c_int32),
     "cr_steer": ([_vp, _vp, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int32),
     "cr_retime": ([_vp, C.POINTER(Problem), C.c_int32, _vp, _vp, _vp], C.c_int32),
+    "cr_rank_seeds": ([_vp, C.POINTER(Problem), C.POINTER(Params), C.c_int32, _vp, _vp, _vp, C.c_float,
+                       C.c_float, C.c_float, C.c_float, _vp, _vp, _vp], C.c_int32),
     "cr_autotune": ([_vp, _vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), C.c_int32,
                      C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                      C.POINTER(C.c_float)], C.c_int32),
@@ -364,17 +366,47 @@ def retime(robot: Robot, problem: ProblemSpec, theta, stream=None):
     return dt
 
 
+RANK_WEIGHTS = dict(w_pose=1.0, w_jerk=1e-3, w_time=1.0, w_dist=0.1)
+
+
+def rank_seeds(robot: Robot, problem: ProblemSpec, theta, cfree, params=None, dt=None, stream=None,
+               **weights):
+    """Scores of the seeds theta (CUDA [B, H, dof]) and the index of the best
+    collision-free one (App. "Solver details"; cr_rank_seeds).  IK mode in
+    params: pose error + distance to q_start; else pose error, largest jerk at
+    dt (CUDA [B], or params' dt) and motion time.  Weights default to
+    RANK_WEIGHTS (the paper gives none).  Returns (score [B], best [1])."""
+    import torch
+    theta = theta.contiguous()
+    B = theta.shape[0]
+    w = dict(RANK_WEIGHTS)
+    w.update(weights)
+    P = params if isinstance(params, Params) else make_params(params)
+    score = torch.empty(B, device=theta.device)
+    best = torch.empty(1, device=theta.device, dtype=torch.int32)
+    cf = cfree.contiguous().to(torch.uint8)
+    pr = problem.struct()
+    check(lib().cr_rank_seeds(robot.handle, C.byref(pr), C.byref(P), int(B), _dptr(theta), _dptr(cf),
+                              _dptr(None if dt is None else dt.contiguous()), float(w["w_pose"]),
+                              float(w["w_jerk"]), float(w["w_time"]), float(w["w_dist"]), _dptr(score),
+                              _dptr(best), _stream(stream)), "cr_rank_seeds")
+    return score, best
+
+
 def time_discretized_solve(ctx, robot: Robot, problem: ProblemSpec, params=None, iters=(100, 100),
                            dt_init=0.25):
     """Alg. "Time Discretization" (App. "Time-step Discretization") for one
     problem: solve at dt_init without the jerk term; retime the best seed to
     dt_opt (the step that puts it at the limits); scale the derivative weights
     to dt_opt and enable jerk; solve again from the first solution at dt_opt;
-    retime the result to dt_f.  Weights on the square of the k-th derivative
-    are multiplied by (dt / dt0)^(2k), dt0 the params' own dt, so each term
-    keeps the magnitude it has for the same trajectory at dt0 (the paper says
-    only that the weights are scaled by the new dt).
-    Returns (SolveOutput, dt_opt, dt_f)."""
+    retime every seed of the result; among the collision-free ones take the
+    lowest blend of pose error, largest jerk and motion time at its own time
+    step (App. "Solver details", rank_seeds).  Weights on the square of the
+    k-th derivative are multiplied by (dt / dt0)^(2k), dt0 the params' own dt,
+    so each term keeps the magnitude it has for the same trajectory at dt0 (the
+    paper says only that the weights are scaled by the new dt).
+    Returns (SolveOutput, dt_opt, dt_f, chosen): dt_f the chosen seed's time
+    step, chosen its index (the solve's own best when no seed is collision-free)."""
     base = params_default()
     if params:
         base.update(params if isinstance(params, dict) else {})
@@ -395,9 +427,12 @@ def time_discretized_solve(ctx, robot: Robot, problem: ProblemSpec, params=None,
     dt_opt = max(dt_opt, 1e-3)
     o2 = solve(ctx, robot, [problem], scaled(dt_opt, True), iters=iters[1],
                device_seeds=[o1.traj.contiguous()])[0]
-    b2 = int(o2.best)
-    dt_f = float(retime(robot, problem, o2.traj[b2:b2 + 1])[0])
-    return o2, dt_opt, dt_f
+    dts = retime(robot, problem, o2.traj)
+    _, chosen = rank_seeds(robot, problem, o2.traj, o2.cfree, scaled(dt_opt, True), dt=dts)
+    b2 = int(chosen)
+    if b2 < 0:
+        b2 = max(int(o2.best), 0)
+    return o2, dt_opt, float(dts[b2]), b2
 
 
 class OptBuffers:
