@@ -377,7 +377,9 @@ def rank_seeds(robot: Robot, problem: ProblemSpec, theta, cfree, params=None, dt
     dt (CUDA [B], or params' dt) and motion time.  Weights default to
     RANK_WEIGHTS (the paper gives none).  Returns (score [B], best [1])."""
     import torch
-    theta = theta.contiguous()
+    theta = theta.to(torch.float32).contiguous()
+    if dt is not None:
+        dt = dt.to(torch.float32).contiguous()
     B = theta.shape[0]
     w = dict(RANK_WEIGHTS)
     w.update(weights)
@@ -387,7 +389,7 @@ def rank_seeds(robot: Robot, problem: ProblemSpec, theta, cfree, params=None, dt
     cf = cfree.contiguous().to(torch.uint8)
     pr = problem.struct()
     check(lib().cr_rank_seeds(robot.handle, C.byref(pr), C.byref(P), int(B), _dptr(theta), _dptr(cf),
-                              _dptr(None if dt is None else dt.contiguous()), float(w["w_pose"]),
+                              _dptr(dt), float(w["w_pose"]),
                               float(w["w_jerk"]), float(w["w_time"]), float(w["w_dist"]), _dptr(score),
                               _dptr(best), _stream(stream)), "cr_rank_seeds")
     return score, best
