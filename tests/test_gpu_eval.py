@@ -207,6 +207,32 @@ def test_eval_ik_small_and_large_launches_agree():
     assert 0 < int(large["cfree"].sum()) < 20000
 
 
+def test_eval_ik_twelve_joints():
+    """IK mode on a 12-joint chain (more links than threads per trajectory in
+    the split form, so a thread owns two links): parity with the oracle in a
+    small launch, and the same bits in a large one."""
+    from scenes import as_f32_robot, as_f32_world
+    rb = as_f32_robot(synth.make_robot((5,) * 12, seed=3, axes=(2, 1) * 6))
+    rng = np.random.default_rng(23)
+    w = as_f32_world(synth.make_world(30, 24))
+    goal = f32(oracle.goal_pose_from_fk(rb, synth.uniform_config(rng, rb)))
+    q = f32(synth.uniform_config(rng, rb, 20000)[:, None, :])
+    pr = synth.Problem(world=w, q_start=f32(synth.uniform_config(rng, rb)), goal=goal, seeds=q[:60])
+    p = dict(flags=crgb.IK_MODE | crgb.SELF)
+    gpu = _gpu_eval(rb, w, pr, q[:60], p)
+    ref = oracle.evaluate(rb, w, pr.q_start, pr.goal, q[:60], p)
+    n_cmp, _ = compare(gpu, ref, label="ik 12 joints")
+    assert n_cmp >= 40
+    R, W = crgb.Robot(rb), crgb.World(w)
+    spec = crgb.ProblemSpec(W, pr.q_start, goal, 1)
+    qd = torch.tensor(q, dtype=torch.float32, device="cuda")
+    small = crgb.evaluate(R, spec, qd[:60].contiguous(), p)
+    large = crgb.evaluate(R, spec, qd, p)
+    torch.cuda.synchronize()
+    for k in ("cost", "grad", "cfree", "terms"):
+        assert torch.equal(small[k], large[k][:60]), k
+
+
 def test_eval_parity_ik_self_contact():
     """IK mode, no boxes: configurations folded onto themselves so that many
     states have penetrating sphere pairs (the self term's argmax and its

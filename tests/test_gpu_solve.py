@@ -160,6 +160,26 @@ def test_ik_small_and_large_batches_agree(ctx):
     assert torch.equal(alone.best, t.best)
 
 
+def test_short_horizon_many_seeds_agree(ctx):
+    """Trajectories of 4 states (28 variables): alone, 8 seeds run one warp
+    each; inside a batch with 4096 more they run one thread each.  Same bits."""
+    rb = scene(spheres=synth.SPHERES_60)[0]
+    R = crgb.Robot(rb)
+    specs = []
+    for k, B in enumerate((8, 4096)):
+        _, w, pr = scene(spheres=synth.SPHERES_60, n_boxes=10, n_seeds=B, horizon=4, world_seed=70 + k,
+                         problem_seed=80 + k)
+        specs.append(_spec(crgb.World(w), pr))
+    together = crgb.solve(ctx, R, specs, None, iters=6, graph=True, persistent=True)
+    torch.cuda.synchronize()
+    alone = crgb.solve(ctx, R, [specs[0]], None, iters=6, graph=False, persistent=False)[0]
+    torch.cuda.synchronize()
+    t = together[0]
+    assert torch.equal(alone.traj, t.traj)
+    assert torch.equal(alone.cost, t.cost)
+    assert torch.equal(alone.best, t.best)
+
+
 def test_solve_result_is_consistent_with_oracle(ctx):
     """Returned best iterates: their oracle cost matches the reported cost
     (1e-4 rel, unless near a decision threshold) and the reported best index
