@@ -34,7 +34,7 @@ constexpr long long kIkSplitBelow = 16384;  // trajectories below which a launch
 // order (costs, gradients) or by an order-free rule (the deepest pair, the
 // collision-free flag), so every TPT gives the same bits.  Large launches use
 // TPT = 1 (throughput), small ones TPT = 8 (latency).
-template <int NT, int TPT>
+template <int NT, int TPT, bool GRAD>
 __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs a) {
   static_assert(TPT == 1 || TPT == 2 || TPT == 4 || TPT == 8 || TPT == 16, "TPT");
   constexpr int kOwn = (kMaxDof + TPT - 1) / TPT;  // links a thread can own
@@ -209,23 +209,29 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
               }
               if (S != 0.f || gs3.x != 0.f || gs3.y != 0.f || gs3.z != 0.f) {
                 cl += prm.w_coll * S;
-                const V3 gx = prm.w_coll * gs3;
+                if (GRAD) {
+                  const V3 gx = prm.w_coll * gs3;
 #pragma unroll
-                for (int j = 0; j < kMaxDof; ++j) {
-                  if (j > l) break;
-                  Gl[j] += joint_share(j, x, gx);
+                  for (int j = 0; j < kMaxDof; ++j) {
+                    if (j > l) break;
+                    Gl[j] += joint_share(j, x, gx);
+                  }
                 }
               }
             }
           }
           if (TPT == 1) {  // links come in order: add at once
             tws += cl;
+            if (GRAD) {
 #pragma unroll
-            for (int j = 0; j < kMaxDof; ++j) g[j] += Gl[j];
+              for (int j = 0; j < kMaxDof; ++j) g[j] += Gl[j];
+            }
           } else {
             c_own[k] = cl;
+            if (GRAD) {
 #pragma unroll
-            for (int j = 0; j < kMaxDof; ++j) G_own[k][j] = Gl[j];
+              for (int j = 0; j < kMaxDof; ++j) G_own[k][j] = Gl[j];
+            }
           }
         }
       }
@@ -235,10 +241,12 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
         for (int l = 0; l < kMaxDof; ++l) {
           if (l >= D) break;
           tws += __shfl_sync(gmask, c_own[l / TPT], l % TPT, TPT);
+          if (GRAD) {
 #pragma unroll
-          for (int j = 0; j < kMaxDof; ++j) {
-            if (j > l) break;
-            g[j] += __shfl_sync(gmask, G_own[l / TPT][j], l % TPT, TPT);
+            for (int j = 0; j < kMaxDof; ++j) {
+              if (j > l) break;
+              g[j] += __shfl_sync(gmask, G_own[l / TPT][j], l % TPT, TPT);
+            }
           }
         }
       }
@@ -361,7 +369,7 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
         }
         if (selfc) {
           ts += prm.w_self * best;
-          if (arg >= 0 && sub == 0) {
+          if (GRAD && arg >= 0 && sub == 0) {
             const uint32_t pr = __ldg(&a.rb.pairs[arg]);
             const int pi = (int)(pr & 0xffffu), pj = (int)(pr >> 16);
             const int li = __ldg(&a.rb.sphere_link[pi]), lj = __ldg(&a.rb.sphere_link[pj]);
@@ -410,26 +418,28 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
           for (int bb = 0; bb < 3; ++bb) tr = fmaf(pv->goal_R[aa * 3 + bb], E[aa * 4 + bb], tr);
         const float dq = (3.f - tr) * 0.25f;
         tg += prm.w_goal_pos * logcoshf(prm.k_goal_pos * rn) + prm.w_goal_rot * logcoshf(prm.k_goal_rot * dq);
-        const float fp = rn > 1e-30f ? prm.w_goal_pos * prm.k_goal_pos * tanhf(prm.k_goal_pos * rn) / rn
-                                     : prm.w_goal_pos * prm.k_goal_pos * prm.k_goal_pos;
-        const V3 dp = fp * e;
-        const float fr = -0.25f * prm.w_goal_rot * prm.k_goal_rot * tanhf(prm.k_goal_rot * dq);
-        // d cost / d R = fr R_g; its effect on joint j is a_j . sum_c R_c x dR_c
-        V3 w = v3(0.f, 0.f, 0.f);
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-          const V3 Rc = v3(E[cc], E[4 + cc], E[8 + cc]);
-          const V3 Gc = fr * v3(pv->goal_R[cc], pv->goal_R[3 + cc], pv->goal_R[6 + cc]);
-          w = w + cross(Rc, Gc);
-        }
-        const V3 pe = v3(E[3], E[7], E[11]);
-#pragma unroll
-        for (int j = 0; j < kMaxDof; ++j) {
-          if (j >= D) break;
-          const float4 r0 = row(j, 0), r1 = row(j, 1), r2 = row(j, 2);
-          const int ax = s_axis[j];
-          const V3 aj = ax == 0 ? v3(r0.x, r1.x, r2.x) : ax == 1 ? v3(r0.y, r1.y, r2.y) : v3(r0.z, r1.z, r2.z);
-          g[j] += dot(dp, cross(aj, pe - v3(r0.w, r1.w, r2.w))) + dot(aj, w);
+        if (GRAD) {
+          const float fp = rn > 1e-30f ? prm.w_goal_pos * prm.k_goal_pos * tanhf(prm.k_goal_pos * rn) / rn
+                                       : prm.w_goal_pos * prm.k_goal_pos * prm.k_goal_pos;
+          const V3 dp = fp * e;
+          const float fr = -0.25f * prm.w_goal_rot * prm.k_goal_rot * tanhf(prm.k_goal_rot * dq);
+          // d cost / d R = fr R_g; its effect on joint j is a_j . sum_c R_c x dR_c
+          V3 w = v3(0.f, 0.f, 0.f);
+  #pragma unroll
+          for (int cc = 0; cc < 3; ++cc) {
+            const V3 Rc = v3(E[cc], E[4 + cc], E[8 + cc]);
+            const V3 Gc = fr * v3(pv->goal_R[cc], pv->goal_R[3 + cc], pv->goal_R[6 + cc]);
+            w = w + cross(Rc, Gc);
+          }
+          const V3 pe = v3(E[3], E[7], E[11]);
+  #pragma unroll
+          for (int j = 0; j < kMaxDof; ++j) {
+            if (j >= D) break;
+            const float4 r0 = row(j, 0), r1 = row(j, 1), r2 = row(j, 2);
+            const int ax = s_axis[j];
+            const V3 aj = ax == 0 ? v3(r0.x, r1.x, r2.x) : ax == 1 ? v3(r0.y, r1.y, r2.y) : v3(r0.z, r1.z, r2.z);
+            g[j] += dot(dp, cross(aj, pe - v3(r0.w, r1.w, r2.w))) + dot(aj, w);
+          }
         }
         if ((flags & CR_CSPACE_GOAL) && pv->has_goal_q) {
           float r2 = 0.f;
@@ -440,11 +450,13 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
             r2 = fmaf(d, d, r2);
           }
           tg += prm.w_cspace * logcoshf(prm.k_cspace * r2);
-          const float cq = 2.f * prm.w_cspace * prm.k_cspace * tanhf(prm.k_cspace * r2);
+          if (GRAD) {
+            const float cq = 2.f * prm.w_cspace * prm.k_cspace * tanhf(prm.k_cspace * r2);
 #pragma unroll
-          for (int j = 0; j < kMaxDof; ++j) {
-            if (j >= D) break;
-            g[j] = fmaf(cq, q[j] - pv->goal_q[j], g[j]);
+            for (int j = 0; j < kMaxDof; ++j) {
+              if (j >= D) break;
+              g[j] = fmaf(cq, q[j] - pv->goal_q[j], g[j]);
+            }
           }
         }
       }
@@ -457,7 +469,7 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
         tb += prm.w_bound * bound_cost(q[j], __ldg(&a.rb.lim[j]), __ldg(&a.rb.lim[D + j]), e2, inv_e2, sl);
         g[j] = fmaf(prm.w_bound, sl, g[j]);
       }
-      if (a.grad) {
+      if (GRAD) {
         float* go = a.grad + vb + (long long)t * D;
 #pragma unroll
         for (int j = 0; j < kMaxDof; ++j) {
@@ -494,11 +506,15 @@ static cudaError_t allow_ik_smem() {
   cudaGetDevice(&dev);
   const unsigned bit = 1u << (dev & 31);
   if (done & bit) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_eval_ik<kIkThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_eval_ik<kIkThreads, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        eval_ik_smem_bytes(kMaxDof));
+  const int lim = eval_ik_smem_bytes(kMaxDof);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_eval_ik<kIkThreads, kIkSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             eval_ik_smem_bytes(kMaxDof));
+    e = cudaFuncSetAttribute(k_eval_ik<kIkThreads, kIkSplit, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_eval_ik<kIkThreads, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_eval_ik<kIkThreads, kIkSplit, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e == cudaSuccess) done |= bit;
   return e;
 }
@@ -506,7 +522,7 @@ static cudaError_t allow_ik_smem() {
 int eval_ik_blocks_per_sm(int dof) {
   int n = 0;
   if (allow_ik_smem() != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval_ik<kIkThreads, 1>, kIkThreads,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval_ik<kIkThreads, 1, true>, kIkThreads,
                                                     eval_ik_smem_bytes(dof)) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
@@ -524,8 +540,12 @@ cudaError_t launch_eval_ik(const EvalArgs& a, cudaStream_t stream) {
   const bool split = n_slots < kIkSplitBelow;
   const long long want = (n_slots * (split ? kIkSplit : 1) + kIkThreads - 1) / kIkThreads;
   const int grid = (int)(want < (1ll << 30) ? want : (1ll << 30));
-  return split ? launch_pdl(k_eval_ik<kIkThreads, kIkSplit>, grid, kIkThreads, (size_t)smem, stream, a)
-               : launch_pdl(k_eval_ik<kIkThreads, 1>, grid, kIkThreads, (size_t)smem, stream, a);
+  // cost-only launches (steering, particles) skip every gradient term
+  if (a.grad)
+    return split ? launch_pdl(k_eval_ik<kIkThreads, kIkSplit, true>, grid, kIkThreads, (size_t)smem, stream, a)
+                 : launch_pdl(k_eval_ik<kIkThreads, 1, true>, grid, kIkThreads, (size_t)smem, stream, a);
+  return split ? launch_pdl(k_eval_ik<kIkThreads, kIkSplit, false>, grid, kIkThreads, (size_t)smem, stream, a)
+               : launch_pdl(k_eval_ik<kIkThreads, 1, false>, grid, kIkThreads, (size_t)smem, stream, a);
 }
 
 }  // namespace crgb

@@ -201,9 +201,14 @@ def test_eval_ik_small_and_large_launches_agree():
     p = dict(flags=crgb.IK_MODE | crgb.SELF)
     small = crgb.evaluate(R, spec, q[:100].contiguous(), p)
     large = crgb.evaluate(R, spec, q, p)
+    # cost-only launches (steering, particles) take the same arithmetic
+    small_nog = crgb.evaluate(R, spec, q[:100].contiguous(), p, want_grad=False)
+    large_nog = crgb.evaluate(R, spec, q, p, want_grad=False)
     torch.cuda.synchronize()
     for k in ("cost", "grad", "cfree", "terms"):
         assert torch.equal(small[k], large[k][:100]), k
+    for k in ("cost", "cfree", "terms"):
+        assert torch.equal(small[k], small_nog[k]) and torch.equal(large[k], large_nog[k]), k
     assert 0 < int(large["cfree"].sum()) < 20000
 
 
