@@ -2,8 +2,8 @@
 // forward kinematics, for sm_103a.
 //
 // One CTA owns a tile of whole trajectories of one problem: a single
-// trajectory for trajectory optimisation (H = 32..128 states), or a group of
-// single-state trajectories for IK.  Everything a trajectory needs stays on
+// trajectory (H = 32..128 states), or several short ones (IK-mode launches
+// go to k_ik.cu instead).  Everything a trajectory needs stays on
 // chip: the link transforms of every state (forward kinematics, Sec. 3.1),
 // the per-(state, sphere) swept world sums and their gradients (Sec. 3.3-3.4,
 // Eq. 10-11), the self-collision argmax per state (Eq. 9), the stencil
