@@ -282,6 +282,36 @@ def cpu_baseline(seconds=10.0):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def profile_ik(crgb, synth, n):
+    """N IK-mode evaluations of 128,000 uniformly drawn configurations of the
+    60-sphere robot against a 40-box world, with gradients (the candidate
+    batch of 1000 goals x 32 seeds x 4 step sizes), inside one NVTX range."""
+    import torch
+    cfg = synth.CONFIGS["ik"]
+    rb = synth.make_robot(cfg.spheres_per_link, seed=0)
+    R = crgb.Robot(rb)
+    rng = np.random.default_rng(3)
+    W = crgb.World(synth.make_world(cfg.n_boxes, cfg.world_seed))
+    qs = synth.uniform_config(rng, rb)
+    goal = np.array([0.3, 0.2, 0.5, 1.0, 0.0, 0.0, 0.0])
+    q = torch.tensor(synth.uniform_config(rng, rb, 128000)[:, None, :], dtype=torch.float32, device="cuda")
+    spec = crgb.ProblemSpec(W, qs, goal, 1)
+    P = crgb.make_params(dict(flags=crgb.IK_MODE | crgb.SELF | crgb.WOLFE))
+    crgb.evaluate(R, spec, q, P, want_terms=False)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("crgb_eval_ik")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(n):
+        crgb.evaluate(R, spec, q, P, want_terms=False)
+    ev1.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_ik": n, "states_per_launch": 128000,
+                      "us_per_launch": ev0.elapsed_time(ev1) / n * 1e3}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -295,6 +325,9 @@ def main():
     ap.add_argument("--profile", type=int, default=0,
                     help="only run N fused evaluations of one line-search batch inside the NVTX "
                          "range crgb_eval (for ncu), then exit")
+    ap.add_argument("--profile-ik", type=int, default=0,
+                    help="only run N IK-mode evaluations of 128,000 states (40 boxes, self-collision, "
+                         "gradients) inside the NVTX range crgb_eval_ik (for ncu), then exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -311,6 +344,9 @@ def main():
         build.build_library()
     if ws > 1:
         dist.barrier()
+
+    if args.profile_ik:
+        return profile_ik(crgb, synth, args.profile_ik)
 
     cfg, rb, R, world, pr = make_workload(crgb, synth, seed_offset=rank)
     W = crgb.World(world)

@@ -172,10 +172,21 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
             const int kc = min(64, K - c0);
             unsigned long long m = 0ull;
             for (int kk = 0; kk < kc; ++kk) {
-              const float4 bc = __ldg(&boxes[c0 + kk].c);
+              const BoxRows* bp = boxes + c0 + kk;
+              const float4 bc = __ldg(&bp->c);
               const float dx = lc.x - bc.x, dy = lc.y - bc.y, dz = lc.z - bc.z;
               const float rb = (reach + bc.w) * 1.0001f + 1e-6f;
-              if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rb * rb) m |= 1ull << kk;
+              // bounding spheres apart: the box test below cannot pass
+              if (!(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rb * rb)) continue;
+              // the link centre's distance to the box: a sphere of the link
+              // within eta of the box puts it within reach
+              const float4 b0 = __ldg(&bp->r0), b1 = __ldg(&bp->r1), b2 = __ldg(&bp->r2), h = __ldg(&bp->h);
+              const float ux = fmaf(b0.x, lc.x, fmaf(b0.y, lc.y, fmaf(b0.z, lc.z, b0.w)));
+              const float uy = fmaf(b1.x, lc.x, fmaf(b1.y, lc.y, fmaf(b1.z, lc.z, b1.w)));
+              const float uz = fmaf(b2.x, lc.x, fmaf(b2.y, lc.y, fmaf(b2.z, lc.z, b2.w)));
+              const float mx = fmaxf(fabsf(ux) - h.x, 0.f), my = fmaxf(fabsf(uy) - h.y, 0.f),
+                          mz = fmaxf(fabsf(uz) - h.z, 0.f);
+              if (fmaf(mx, mx, fmaf(my, my, mz * mz)) < reach * reach) m |= 1ull << kk;
             }
             if (!m) continue;
             for (int qq = s0; qq < s1; ++qq) {
@@ -193,6 +204,12 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
                 const float ux = fmaf(b0.x, x.x, fmaf(b0.y, x.y, fmaf(b0.z, x.z, b0.w)));
                 const float uy = fmaf(b1.x, x.x, fmaf(b1.y, x.y, fmaf(b1.z, x.z, b1.w)));
                 const float uz = fmaf(b2.x, x.x, fmaf(b2.y, x.y, fmaf(b2.z, x.z, b2.w)));
+                {  // farther than radius + eta outside the box: no term, and clear
+                  const float mx = fmaxf(fabsf(ux) - h.x, 0.f), my = fmaxf(fabsf(uy) - h.y, 0.f),
+                              mz = fmaxf(fabsf(uz) - h.z, 0.f);
+                  const float thr = c.w + eta;
+                  if (fmaf(mx, mx, fmaf(my, my, mz * mz)) >= thr * thr) continue;
+                }
                 V3 gu;
                 const float phi = sdf_local(ux, uy, uz, h, gu);
                 if (!(phi - c.w > 0.f)) free_ok = false;  // clearance of the waypoint
