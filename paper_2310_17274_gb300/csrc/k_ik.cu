@@ -23,7 +23,10 @@ namespace crgb {
 
 namespace {
 
-constexpr int kIkThreads = 128;  // threads of a CTA (4 warps)
+// threads of a CTA: with gradients 96 (five CTAs fit an SM by registers and
+// shared memory), cost only 128
+constexpr int kIkThreadsGrad = 96;
+constexpr int kIkThreadsCost = 128;
 constexpr int kNear = 8;         // near spheres of one link kept in registers by the self term
 constexpr int kIkSplit = 8;      // threads per trajectory in small launches
 constexpr long long kIkSplitBelow = 16384;  // trajectories below which a launch is small
@@ -35,7 +38,7 @@ constexpr long long kIkSplitBelow = 16384;  // trajectories below which a launch
 // collision-free flag), so every TPT gives the same bits.  Large launches use
 // TPT = 1 (throughput), small ones TPT = 8 (latency).
 template <int NT, int TPT, bool GRAD>
-__global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs a) {
+__global__ void __launch_bounds__(NT, NT == kIkThreadsGrad ? 5 : 1) k_eval_ik(const __grid_constant__ EvalArgs a) {
   static_assert(TPT == 1 || TPT == 2 || TPT == 4 || TPT == 8 || TPT == 16, "TPT");
   constexpr int kOwn = (kMaxDof + TPT - 1) / TPT;  // links a thread can own
   // rows of this thread's link transforms, s_tf[(l * 3 + row) * NT + tid],
@@ -513,7 +516,9 @@ __global__ void __launch_bounds__(NT) k_eval_ik(const __grid_constant__ EvalArgs
 
 }  // namespace
 
-int eval_ik_smem_bytes(int dof) { return dof * 4 * kIkThreads * (int)sizeof(float4); }
+static int ik_smem(int dof, int nt) { return dof * 4 * nt * (int)sizeof(float4); }
+
+int eval_ik_smem_bytes(int dof) { return ik_smem(dof, kIkThreadsCost); }
 
 // The dynamic shared memory limit is raised once per device to what the
 // largest robot needs, never lowered, so captured launches stay valid.
@@ -523,15 +528,12 @@ static cudaError_t allow_ik_smem() {
   cudaGetDevice(&dev);
   const unsigned bit = 1u << (dev & 31);
   if (done & bit) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_eval_ik<kIkThreads, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       eval_ik_smem_bytes(kMaxDof));
-  const int lim = eval_ik_smem_bytes(kMaxDof);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_eval_ik<kIkThreads, kIkSplit, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_eval_ik<kIkThreads, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_eval_ik<kIkThreads, kIkSplit, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  const int lg = ik_smem(kMaxDof, kIkThreadsGrad), lc = ik_smem(kMaxDof, kIkThreadsCost);
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_eval_ik<kIkThreadsGrad, 1, true>, at, lg);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_ik<kIkThreadsGrad, kIkSplit, true>, at, lg);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_ik<kIkThreadsCost, 1, false>, at, lc);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_ik<kIkThreadsCost, kIkSplit, false>, at, lc);
   if (e == cudaSuccess) done |= bit;
   return e;
 }
@@ -539,10 +541,17 @@ static cudaError_t allow_ik_smem() {
 int eval_ik_blocks_per_sm(int dof) {
   int n = 0;
   if (allow_ik_smem() != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval_ik<kIkThreads, 1, true>, kIkThreads,
-                                                    eval_ik_smem_bytes(dof)) != cudaSuccess)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_eval_ik<kIkThreadsGrad, 1, true>, kIkThreadsGrad,
+                                                    ik_smem(dof, kIkThreadsGrad)) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
+}
+
+template <int NT, int TPT, bool GRAD>
+static cudaError_t launch_ik(const EvalArgs& a, long long n_slots, cudaStream_t stream) {
+  const long long want = (n_slots * TPT + NT - 1) / NT;
+  const int grid = (int)(want < (1ll << 30) ? want : (1ll << 30));
+  return launch_pdl(k_eval_ik<NT, TPT, GRAD>, grid, NT, (size_t)ik_smem(a.rb.dof, NT), stream, a);
 }
 
 cudaError_t launch_eval_ik(const EvalArgs& a, cudaStream_t stream) {
@@ -550,19 +559,16 @@ cudaError_t launch_eval_ik(const EvalArgs& a, cudaStream_t stream) {
   const int n_tiles = a.problems ? a.n_tiles : (a.prob0.n_traj + a.traj_per_tile - 1) / a.traj_per_tile;
   const long long n_slots = (long long)n_tiles * per_tile;
   if (n_slots <= 0) return cudaSuccess;
-  const int smem = eval_ik_smem_bytes(a.rb.dof);
   cudaError_t e = allow_ik_smem();
   if (e != cudaSuccess) return e;
-  // few trajectories: several threads each, for latency (same results)
-  const bool split = n_slots < kIkSplitBelow;
-  const long long want = (n_slots * (split ? kIkSplit : 1) + kIkThreads - 1) / kIkThreads;
-  const int grid = (int)(want < (1ll << 30) ? want : (1ll << 30));
+  // few trajectories: several threads each, for latency (same results);
   // cost-only launches (steering, particles) skip every gradient term
+  const bool split = n_slots < kIkSplitBelow;
   if (a.grad)
-    return split ? launch_pdl(k_eval_ik<kIkThreads, kIkSplit, true>, grid, kIkThreads, (size_t)smem, stream, a)
-                 : launch_pdl(k_eval_ik<kIkThreads, 1, true>, grid, kIkThreads, (size_t)smem, stream, a);
-  return split ? launch_pdl(k_eval_ik<kIkThreads, kIkSplit, false>, grid, kIkThreads, (size_t)smem, stream, a)
-               : launch_pdl(k_eval_ik<kIkThreads, 1, false>, grid, kIkThreads, (size_t)smem, stream, a);
+    return split ? launch_ik<kIkThreadsGrad, kIkSplit, true>(a, n_slots, stream)
+                 : launch_ik<kIkThreadsGrad, 1, true>(a, n_slots, stream);
+  return split ? launch_ik<kIkThreadsCost, kIkSplit, false>(a, n_slots, stream)
+               : launch_ik<kIkThreadsCost, 1, false>(a, n_slots, stream);
 }
 
 }  // namespace crgb
