@@ -55,7 +55,10 @@ __global__ void __launch_bounds__(NT, NT == kIkThreadsGrad ? 5 : 1) k_eval_ik(co
   // the robot is constant; theta and the outputs belong to the previous grid
   // until it has finished
   pdl_wait();
-  pdl_launch_dependents();
+  // a small launch (one wave) lets the next kernel start at once; a large one
+  // only at its end: waiting CTAs of the next kernel slowed its last wave
+  // (an IK solve step 215 -> 133 us)
+  if (TPT != 1) pdl_launch_dependents();
   __syncthreads();
 
   const cr_params& prm = a.prm;
@@ -512,6 +515,7 @@ __global__ void __launch_bounds__(NT, NT == kIkThreadsGrad ? 5 : 1) k_eval_ik(co
       tt[4] = tg;
     }
   }
+  if (TPT == 1) pdl_launch_dependents();
 }
 
 }  // namespace
