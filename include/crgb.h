@@ -40,9 +40,10 @@ typedef int32_t cr_status;
 #define CR_EINVAL 1    /* bad argument or size */
 #define CR_ENOMEM 2    /* device or host allocation failed */
 #define CR_ECUDA 3     /* a CUDA call failed (message has the CUDA error) */
-#define CR_ETIMEOUT 4  /* a bounded device wait gave up */
-#define CR_EBUSY 5     /* admission refused: not enough free device memory */
-#define CR_ENAN 6      /* a seed produced a non-finite cost */
+#define CR_ETIMEOUT 4  /* reserved: no call of this library waits on the device */
+#define CR_EBUSY 5     /* reserved: the server queues a request that does not fit yet */
+#define CR_ENAN 6      /* reserved: a non-finite cost is reported in the cost outputs (NaN never
+                          wins the best seed), not as a status */
 
 #define CR_MAX_DOF 16
 #define CR_MAX_ALPHA 16
