@@ -531,7 +531,8 @@ def main():
 def bench_ik(crgb, synth, ctx, R, rb, n_goals=1000, n_seeds=32, iters=50, collision=True):
     """Batched IK: 1000 goals x 32 seeds (H = 1) in one solve.  With
     collision: 40 cuboids, self-collision on, goals from FK of collision-free
-    configurations; without: no cuboids, no self term (the paper's plain IK).
+    configurations; without: no cuboids, no self term and no self check in
+    the collision-free flag (the paper's IK without collision checking).
     Solved (Sec. 6's 5 mm / 5 % test): the best seed is collision-free, within
     5 mm, and its orientation distance d_q = (3 - tr(R_g^T R)) / 4 of Eq. 14 is
     at most 1e-3 (about 3.6 degrees); the looser reading d_q <= 0.05 (5 % of
@@ -541,13 +542,16 @@ def bench_ik(crgb, synth, ctx, R, rb, n_goals=1000, n_seeds=32, iters=50, collis
     rng = np.random.default_rng(3)
     qs = synth.uniform_config(rng, rb)
     flags = crgb.IK_MODE | crgb.WOLFE | (crgb.SELF if collision else 0)
-    ikp = crgb.make_params(dict(flags=flags, alpha=list(cfg.alphas)))
+    # goals and box rejection use the full validity check (self-collision
+    # included); the plain solve checks no collision at all (Sec. 6)
+    checkp = crgb.make_params(dict(flags=flags, alpha=list(cfg.alphas)))
+    ikp = crgb.make_params(dict(flags=flags | (0 if collision else crgb.NO_SELF_CHECK), alpha=list(cfg.alphas)))
 
     def reject(pose, he):
         W1 = crgb.World(synth.World(pose=pose[None], half_ext=he[None]))
         spec = crgb.ProblemSpec(W1, qs, np.array([0, 0, 0, 1.0, 0, 0, 0]), 1)
         out = crgb.evaluate(R, spec, torch.tensor(qs, dtype=torch.float32, device="cuda").view(1, 1, -1),
-                            ikp, want_grad=False, want_terms=False)
+                            checkp, want_grad=False, want_terms=False)
         return not bool(out["cfree"][0])
 
     world = synth.make_world(cfg.n_boxes if collision else 0, cfg.world_seed, reject)
@@ -559,7 +563,7 @@ def bench_ik(crgb, synth, ctx, R, rb, n_goals=1000, n_seeds=32, iters=50, collis
     while len(qg) < n_goals:
         cand = synth.uniform_config(rng, rb, 4096)
         ev = crgb.evaluate(R, probe, torch.tensor(cand[:, None, :], dtype=torch.float32, device="cuda"),
-                           ikp, want_grad=False, want_terms=False)
+                           checkp, want_grad=False, want_terms=False)
         qg = np.concatenate([qg, cand[ev["cfree"].cpu().numpy().astype(bool)]])
     qg = qg[:n_goals]
     _, ee, _ = crgb.fk(R, torch.tensor(qg, dtype=torch.float32, device="cuda"), spheres=False)

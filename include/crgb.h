@@ -59,6 +59,8 @@ typedef int32_t cr_status;
 #define CR_IK_MODE 32u       /* single-state problems: no stencil terms, no sweep, no speed */
 #define CR_VEL_COST 64u      /* velocity log-cosh term of Eq. 16 on every sample */
 #define CR_CSPACE_GOAL 128u  /* joint-space goal cost of Eq. 15 (problems with goal_q) */
+#define CR_NO_SELF_CHECK 256u /* IK mode without CR_SELF: the collision-free flag leaves out self-collision
+                                 (IK without collision checking, Sec. 6); EINVAL in any other mode */
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* cr_last_error(void);

@@ -547,9 +547,12 @@ static void eval_one(const cro_robot* rb, const box_t* boxes, int32_t K, const d
     }
   }
 
-  /* Eq. 9 self term per state */
+  /* Eq. 9 self term per state (skipped whole when the caller asks for no
+   * self check: IK mode without the self term, Sec. 6's IK without collision
+   * checking) */
   double* gself = (double*)calloc((size_t)M * 3, sizeof(double));
-  for (int t = 1; t <= H; ++t) {
+  const int self_check = !(ik && !(prm->flags & CRO_SELF) && (prm->flags & CRO_NO_SELF_CHECK));
+  for (int t = 1; t <= H && self_check; ++t) {
     const double* Xt = X + (size_t)t * M * 4;
     int32_t arg;
     double pen = cro_self_penetration(rb, Xt, &arg, gself);

@@ -34,6 +34,7 @@ extern "C" {
 #define CRO_IK_MODE      32u  /* single-state problem: no stencil terms, no sweep, no speed */
 #define CRO_VEL_COST     64u  /* velocity logcosh of Eq. 16 over all samples (Q = all) */
 #define CRO_CSPACE_GOAL  128u /* Eq. 15 joint-space goal cost (needs goal_q) */
+#define CRO_NO_SELF_CHECK 256u /* IK mode without CRO_SELF: no self-collision in the validity flag */
 
 /* Robot: serial revolute chain + sphere model (Sec. 3.1, App. E.1 kinematics data). */
 typedef struct {

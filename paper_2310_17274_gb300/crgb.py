@@ -18,6 +18,7 @@ _lock = threading.Lock()
 _lib = None
 
 SWEPT, SPEED, SELF, WOLFE, STRONG_WOLFE, IK_MODE, VEL_COST, CSPACE_GOAL = 1, 2, 4, 8, 16, 32, 64, 128
+NO_SELF_CHECK = 256
 N_TERMS = 5
 MAX_ALPHA = 16
 

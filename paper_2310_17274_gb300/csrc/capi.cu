@@ -333,6 +333,8 @@ cr_status check_params(const cr_params* p) {
   if (!(p->eta > 0) || !(p->eta_bound > 0) || !(p->dt > 0))
     return fail(CR_EINVAL, "eta, eta_bound and dt must be > 0");
   if (p->sweep_steps < 0 || p->sweep_steps > 64) return fail(CR_EINVAL, "sweep_steps outside 0..64");
+  if ((p->flags & CR_NO_SELF_CHECK) && (!(p->flags & CR_IK_MODE) || (p->flags & CR_SELF)))
+    return fail(CR_EINVAL, "CR_NO_SELF_CHECK needs CR_IK_MODE without CR_SELF");
   return CR_OK;
 }
 

@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(NT, NT == kIkThreadsGrad ? 5 : 1) k_eval_ik(co
       // has both), else every listed pair of the link pair.  The deepest
       // penetration wins, the first pair of the caller's list on exact ties;
       // every listed pair counts for the collision-free flag.
-      if (P > 0) {
+      if (P > 0 && !(flags & CR_NO_SELF_CHECK)) {
         float best = 0.f;
         int arg = -1;
         auto take = [&](float pen, int p) {

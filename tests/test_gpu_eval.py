@@ -259,6 +259,34 @@ def test_eval_parity_ik_self_contact():
     assert hit.sum() >= 20 and (~hit).sum() >= 20, hit.sum()
 
 
+def test_eval_ik_without_self_check():
+    """IK without collision checking: the no-self-check flag drops self contact
+    from the collision-free flag (parity with the oracle on folded
+    configurations, costs unchanged) and is refused outside IK mode or with
+    the self term on."""
+    rb, w, _ = scene(spheres=synth.SPHERES_60, n_boxes=0)
+    rng = np.random.default_rng(14)
+    lo, hi = np.asarray(rb.q_lo), np.asarray(rb.q_hi)
+    u = rng.uniform(0.0, 1.0, (200, rb.dof)) ** 0.25 * np.where(rng.uniform(size=(200, rb.dof)) < 0.5, -1, 1)
+    q = f32(0.5 * (lo + hi) + 0.5 * (hi - lo) * u)[:, None, :]
+    goal = f32(oracle.goal_pose_from_fk(rb, synth.uniform_config(rng, rb)))
+    pr = synth.Problem(world=w, q_start=f32(synth.uniform_config(rng, rb)), goal=goal, seeds=q)
+    p = dict(flags=crgb.IK_MODE | crgb.NO_SELF_CHECK)
+    gpu = _gpu_eval(rb, w, pr, q, p)
+    ref = oracle.evaluate(rb, w, pr.q_start, pr.goal, q, p)
+    compare(gpu, ref, label="ik no self check")
+    assert gpu["cfree"].all()
+    plain = _gpu_eval(rb, w, pr, q, dict(flags=crgb.IK_MODE))
+    assert not plain["cfree"].all()
+    np.testing.assert_array_equal(plain["cost"], gpu["cost"])
+    R, W = crgb.Robot(rb), crgb.World(w)
+    spec = crgb.ProblemSpec(W, pr.q_start, goal, 1)
+    th = torch.tensor(q, dtype=torch.float32, device="cuda")
+    for bad in (crgb.NO_SELF_CHECK, crgb.IK_MODE | crgb.SELF | crgb.NO_SELF_CHECK):
+        with pytest.raises(crgb.CrError):
+            crgb.evaluate(R, spec, th, dict(flags=bad))
+
+
 def test_eval_many_boxes_and_max_horizon():
     """More boxes than one shared-memory chunk (150 > 64) and the largest horizon."""
     rb, w, pr = scene(n_boxes=150, n_seeds=2, horizon=128, world_seed=8, problem_seed=3)

@@ -1026,3 +1026,32 @@ def test_rank_seeds_closed_forms_and_choice(oracle_mod):
     assert np.isnan(s[2]) and b == 1
     _, b = oracle_mod.rank_seeds(rb, qg, goal, th4, [0, 0, 0, 0], dt_all=0.05)
     assert b == -1
+
+
+def test_ik_without_self_check(oracle_mod):
+    """IK without collision checking (Sec. 6): with the self term off and the
+    no-self-check flag, a configuration folded onto itself is reported free
+    when no box is near, and its cost is unchanged; without the flag the same
+    configuration is not free."""
+    rb = synth.make_robot(synth.SPHERES_60, seed=0)
+    rng = np.random.default_rng(42)
+    lo, hi = np.asarray(rb.q_lo), np.asarray(rb.q_hi)
+    world = synth.World(pose=np.zeros((0, 7)), half_ext=np.zeros((0, 3)))
+    goal = oracle_mod.goal_pose_from_fk(rb, synth.uniform_config(rng, rb))
+    q0 = synth.uniform_config(rng, rb)
+    found = None
+    for _ in range(200):
+        u = rng.uniform(0.0, 1.0, rb.dof) ** 0.25 * np.where(rng.uniform(size=rb.dof) < 0.5, -1, 1)
+        q = 0.5 * (lo + hi) + 0.5 * (hi - lo) * u
+        _, sph, _ = oracle_mod.fk(rb, q)
+        pen, _, _ = oracle_mod.self_penetration(rb, sph)
+        if pen > 1e-3:
+            found = q
+            break
+    assert found is not None
+    th = found[None, None, :]
+    plain = oracle_mod.evaluate(rb, world, q0, goal, th, dict(flags=oracle_mod.IK_MODE))
+    nocheck = oracle_mod.evaluate(rb, world, q0, goal, th,
+                                  dict(flags=oracle_mod.IK_MODE | oracle_mod.NO_SELF_CHECK))
+    assert not plain["cfree"][0] and nocheck["cfree"][0]
+    assert nocheck["cost"][0] == plain["cost"][0]
