@@ -636,6 +636,178 @@ __global__ void __launch_bounds__(128) k_opt_lane(const __grid_constant__ OptArg
   }
 }
 
+// Seeds of at most 8 variables (IK of arms with up to 8 joints), eight lanes
+// per seed, lane k holding element k.  The one-warp kernel's sum of 32 lanes
+// has +0 in lanes 8..31, so lane 0's butterfly adds +0 twice to each of the
+// first eight partials before the levels 4, 2, 1 that combine them; the
+// eight-lane group does exactly that, then the same virtual-warp sum, so the
+// results are bit-identical to the other widths.
+__device__ __forceinline__ float g8_dot(float a, float b, bool live, unsigned gm) {
+  float v = live ? fmaf(a, b, 0.f) : 0.f;
+  v = (v + 0.f) + 0.f;
+  v += __shfl_xor_sync(gm, v, 4, 8);
+  v += __shfl_xor_sync(gm, v, 2, 8);
+  v += __shfl_xor_sync(gm, v, 1, 8);
+  float s = 0.f;
+  s += v;
+#pragma unroll
+  for (int w = 1; w < kVirt / 32; ++w) s += 0.f;
+  return s;
+}
+
+__global__ void __launch_bounds__(128) k_opt_g8(const __grid_constant__ OptArgs a) {
+  const int D = a.dof, m = a.prm.history, na = a.prm.n_alpha;
+  const cr_opt_state& st = a.st;
+  const int k = threadIdx.x & 7;
+  const unsigned gm = 0xffu << (threadIdx.x & 24);
+  pdl_wait();
+  pdl_launch_dependents();
+  if (a.reset_queue && blockIdx.x == 0 && threadIdx.x == 0) *a.reset_queue = 0;
+  const int groups = gridDim.x * (blockDim.x >> 3);
+  // the eight lanes of a seed take the same trip through this loop
+  for (int bt = (blockIdx.x * blockDim.x + threadIdx.x) >> 3; bt < a.n_seeds; bt += groups) {
+    int n, vo, b;
+    if (a.seed_tab) {
+      const int4 e = a.seed_tab[bt];
+      n = e.x;
+      vo = e.y;
+      b = e.z;
+    } else {
+      n = a.horizon * D;
+      vo = bt * n;
+      b = bt;
+    }
+    const bool live = k < n;
+    float* x = st.x + vo;
+    float* g = st.g + vo;
+    float xr = live ? x[k] : 0.f, gr = live ? g[k] : 0.f;
+
+    // ---------------- line-search selection (Alg. 1) ----------------
+    if (a.do_select) {
+      const float dr = live ? st.dir[vo + k] : 0.f;
+      const float* cand = st.cand + (long long)vo * na;
+      const float* cgrad = st.cand_grad + (long long)vo * na;
+      const float c0 = st.c[b];
+      const float gd0 = g8_dot(gr, dr, live, gm);
+      int idx = 0;
+      float cnew = st.cand_cost[b * na];
+      for (int l = 0; l < na; ++l) {
+        const float cl = st.cand_cost[b * na + l];
+        bool ok = cl <= c0 + a.prm.armijo_c1 * a.prm.alpha[l] * gd0;
+        if (a.prm.flags & CR_WOLFE) {
+          const float gl = live ? cgrad[(long long)l * n + k] : 0.f;
+          const float gld = g8_dot(gl, dr, live, gm);
+          if (a.prm.flags & CR_STRONG_WOLFE)
+            ok = ok && fabsf(gld) <= a.prm.wolfe_c2 * fabsf(gd0);
+          else
+            ok = ok && gld >= a.prm.wolfe_c2 * gd0;
+        }
+        if (ok) {  // largest passing index; 0 when none passes
+          idx = l;
+          cnew = cl;
+        }
+      }
+      const bool better = cnew < st.best_c[b];  // NaN never improves the best
+      if (live) {
+        xr = cand[(long long)idx * n + k];
+        gr = cgrad[(long long)idx * n + k];
+        x[k] = xr;
+        g[k] = gr;
+        if (better) st.best_x[vo + k] = xr;
+      }
+      __syncwarp(gm);  // every lane has read best_c before lane 0 writes it
+      if (k == 0) {
+        st.c[b] = cnew;
+        st.ls_index[b] = idx;
+        if (better) {
+          st.best_c[b] = cnew;
+          st.best_cfree[b] = st.cand_cfree[b * na + idx];
+        }
+      }
+    }
+    if (a.init_best) {
+      if (live) st.best_x[vo + k] = xr;
+      __syncwarp(gm);
+      if (k == 0) st.best_c[b] = st.c[b];
+    }
+
+    // ---------------- L-BFGS step (App. A.7) ----------------
+    if (a.do_propose) {
+      float* s_g = st.s + (long long)vo * m;
+      float* y_g = st.y + (long long)vo * m;
+      float* rho_g = st.rho + b * m;
+      const int it = st.iter[b];
+      int shift = 0;
+      __syncwarp(gm);  // every lane has read iter and rho before lane 0 writes them
+      if (it > 0) {
+        const int w = (it - 1) % m;
+        const float xp = live ? st.x_prev[vo + k] : 0.f, gp = live ? st.g_prev[vo + k] : 0.f;
+        const float sv = live ? xr - xp : 0.f, yv = live ? gr - gp : 0.f;
+        if (live) {
+          s_g[(long long)w * n + k] = sv;
+          y_g[(long long)w * n + k] = yv;
+        }
+        const float ys = g8_dot(yv, sv, live, gm);
+        if (k == 0) rho_g[w] = ys > 1e-8f ? 1.f / ys : 0.f;
+        shift = it % m;
+      }
+      if (live) {
+        st.x_prev[vo + k] = xr;
+        st.g_prev[vo + k] = gr;
+      }
+      __syncwarp(gm);  // the new pair and its rho are visible to the group
+      if (k == 0) st.iter[b] = it + 1;
+
+      // two-loop recursion: q = g; newest to oldest
+      float q = gr;
+      float alpha[CR_MAX_HISTORY];
+      for (int i = m - 1; i >= 0; --i) {
+        const int p = (i + shift) % m;
+        const float rho = rho_g[p];
+        if (rho == 0.f) {  // inert pair: alpha = 0, q unchanged
+          alpha[i] = 0.f;
+          continue;
+        }
+        const float sp = live ? s_g[(long long)p * n + k] : 0.f, yp = live ? y_g[(long long)p * n + k] : 0.f;
+        const float al = rho * g8_dot(sp, q, live, gm);
+        alpha[i] = al;
+        if (live) q = fmaf(-al, yp, q);
+      }
+      // H0 = gamma I from the newest valid pair
+      float gamma = 1.f;
+      for (int i = m - 1; i >= 0; --i) {
+        const int p = (i + shift) % m;
+        if (rho_g[p] > 0.f) {
+          const float sp = live ? s_g[(long long)p * n + k] : 0.f, yp = live ? y_g[(long long)p * n + k] : 0.f;
+          gamma = g8_dot(sp, yp, live, gm) / g8_dot(yp, yp, live, gm);
+          break;
+        }
+      }
+      q *= gamma;
+      for (int i = 0; i < m; ++i) {
+        const int p = (i + shift) % m;
+        const float rho = rho_g[p];
+        if (rho == 0.f) continue;
+        const float sp = live ? s_g[(long long)p * n + k] : 0.f, yp = live ? y_g[(long long)p * n + k] : 0.f;
+        const float coef = alpha[i] - rho * g8_dot(yp, q, live, gm);
+        if (live) q = fmaf(sp, coef, q);
+      }
+      // direction and the clipped candidates of Alg. 1
+      if (live) {
+        const float dk = -q;
+        st.dir[vo + k] = dk;
+        float* cand = st.cand + (long long)vo * na;
+        const float lo = a.q_lo[k % D], hi = a.q_hi[k % D];
+        for (int l = 0; l < na; ++l) {
+          float v = fmaf(a.prm.alpha[l], dk, xr);
+          v = fminf(fmaxf(v, lo), hi);
+          cand[(long long)l * n + k] = v;
+        }
+      }
+    }
+  }
+}
+
 // The largest dynamic shared memory any launch may ask for is set once per
 // kernel and device (never lowered), so launches captured in a graph stay
 // valid whatever is launched later.
@@ -673,7 +845,10 @@ cudaError_t launch_opt(const OptArgs& a, int n_max, cudaStream_t stream) {
   // few: one warp per seed (latency); both give the same bits
   if (n_max <= 32 && a.n_seeds >= kLaneSeedsFrom) {
     const int grid = (a.n_seeds + 127) / 128;
-    if (n_max <= 8) return launch_pdl(k_opt_lane<8>, grid, 128, 0, stream, a);
+    if (n_max <= 8) {
+      const long long g8 = ((long long)a.n_seeds * 8 + 127) / 128;
+      return launch_pdl(k_opt_g8, (int)(g8 < (1ll << 30) ? g8 : (1ll << 30)), 128, 0, stream, a);
+    }
     if (n_max <= 16) return launch_pdl(k_opt_lane<16>, grid, 128, 0, stream, a);
     return launch_pdl(k_opt_lane<32>, grid, 128, 0, stream, a);
   }
