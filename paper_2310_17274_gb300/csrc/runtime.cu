@@ -461,12 +461,17 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
   // tables through a pinned staging buffer; the previous call's copy out of
   // it must have finished before it is rewritten
   if (ctx->staged) RT_CUDA(cudaEventSynchronize(ctx->staged));
-  if (ctx->tab_pinned_bytes < pl.tab_bytes) {
+  // host seeds are gathered behind the tables and copied in one piece (the x
+  // region holds the problems' seeds back to back)
+  const bool host_seeds = !(solve_flags & CR_SOLVE_DEVICE_SEEDS);
+  const size_t seed_off = (pl.tab_bytes + 255) & ~size_t(255);
+  const size_t staged_bytes = host_seeds ? seed_off + (size_t)pl.V * 4 : pl.tab_bytes;
+  if (ctx->tab_pinned_bytes < staged_bytes) {
     if (ctx->tab_pinned) cudaFreeHost(ctx->tab_pinned);
     ctx->tab_pinned = nullptr;
     ctx->tab_pinned_bytes = 0;
-    RT_CUDA(cudaMallocHost(&ctx->tab_pinned, pl.tab_bytes));
-    ctx->tab_pinned_bytes = pl.tab_bytes;
+    RT_CUDA(cudaMallocHost(&ctx->tab_pinned, staged_bytes));
+    ctx->tab_pinned_bytes = staged_bytes;
   }
   if (!ctx->staged) RT_CUDA(cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming));
   unsigned char* h = ctx->tab_pinned;
@@ -477,15 +482,21 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
   std::memcpy(h + pl.o_seed, pl.seedtab.data(), pl.seedtab.size() * sizeof(int4));
   std::memcpy(h + pl.o_res, pl.results.data(), pl.P * sizeof(ResultView));
   RT_CUDA(cudaMemcpyAsync(tab, h, pl.tab_bytes, cudaMemcpyHostToDevice, st));
-  RT_CUDA(cudaEventRecord(ctx->staged, st));
   // seeds -> x (host memory, or device memory with CR_SOLVE_DEVICE_SEEDS)
-  const cudaMemcpyKind kind =
-      (solve_flags & CR_SOLVE_DEVICE_SEEDS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  for (int p = 0; p < n_problems; ++p) {
-    const size_t bytes = (size_t)problems[p].n_seeds * problems[p].horizon * robot->dof * 4;
-    RT_CUDA(cudaMemcpyAsync(ws + pl.o_x + (size_t)pl.probs_x[p].var_base * 4, problems[p].seeds, bytes,
-                            kind, st));
+  if (host_seeds) {
+    for (int p = 0; p < n_problems; ++p) {
+      const size_t bytes = (size_t)problems[p].n_seeds * problems[p].horizon * robot->dof * 4;
+      std::memcpy(h + seed_off + (size_t)pl.probs_x[p].var_base * 4, problems[p].seeds, bytes);
+    }
+    RT_CUDA(cudaMemcpyAsync(ws + pl.o_x, h + seed_off, (size_t)pl.V * 4, cudaMemcpyHostToDevice, st));
+  } else {
+    for (int p = 0; p < n_problems; ++p) {
+      const size_t bytes = (size_t)problems[p].n_seeds * problems[p].horizon * robot->dof * 4;
+      RT_CUDA(cudaMemcpyAsync(ws + pl.o_x + (size_t)pl.probs_x[p].var_base * 4, problems[p].seeds, bytes,
+                              cudaMemcpyDeviceToDevice, st));
+    }
   }
+  RT_CUDA(cudaEventRecord(ctx->staged, st));
   const bool persistent = (solve_flags & CR_SOLVE_PERSISTENT) != 0;
   if (!(solve_flags & CR_SOLVE_GRAPH)) {
     return enqueue_iterations(ctx, robot, params, pl, ws, tab, iters, persistent, st);
