@@ -108,6 +108,9 @@ def lib():
         L.cro_eval.argtypes = [C.POINTER(_Robot), C.POINTER(_World), _dp, _dp, _dp,
                                C.POINTER(_Params), C.c_int32, _dp, C.c_int32, _dp, _dp, _up,
                                _dp, _dp]
+        L.cro_eval_states.argtypes = [C.POINTER(_Robot), C.POINTER(_World), _dp, _dp, _dp,
+                                      C.POINTER(_Params), C.c_int32, _dp, C.c_int32, _dp, _dp, _up,
+                                      _dp, _dp, _dp, _dp, _dp]
         L.cro_lbfgs_direction.argtypes = [C.POINTER(_Lbfgs), _dp]
         L.cro_ls_candidates.argtypes = [C.POINTER(_Params), C.c_int32, C.c_int32, _dp, _dp,
                                         _dp, _dp, _dp]
@@ -306,9 +309,13 @@ def goal_cost(params, ee, goal7):
 # whole evaluation and optimiser
 # ---------------------------------------------------------------------------
 
-def evaluate(rb, world, q_start, goal7, theta, params=None, want_grad=True, goal_q=None):
+def evaluate(rb, world, q_start, goal7, theta, params=None, want_grad=True, goal_q=None, states=False):
     """Cost, gradient, collision-free flag, per-term costs and decision margin
-    of trajectories theta [B,H,dof] (one problem)."""
+    of trajectories theta [B,H,dof] (one problem).  With states=True also the
+    per-state outputs of cro_eval_states: state_terms [B,H,2] (world, self
+    cost of each state), state_margin [B,H] (distance of the state's cost- and
+    gradient-setting decisions from their thresholds) and state_clear [B,H]
+    (the state's smallest clearance; collision-free when > 0)."""
     keep = _Keep()
     R = _robot(rb, keep)
     W = _world(world, keep)
@@ -321,9 +328,18 @@ def evaluate(rb, world, q_start, goal7, theta, params=None, want_grad=True, goal
     terms = np.zeros((B, N_TERMS))
     margin = np.zeros(B)
     gq = None if goal_q is None else _f64(goal_q)
-    lib().cro_eval(C.byref(R), C.byref(W), _p(_f64(q_start)), _p(_f64(goal7)), _p(gq), C.byref(P),
-                   H, _p(th), B, _p(cost), _p(grad), _p(cfree, _up), _p(terms), _p(margin))
-    return dict(cost=cost, grad=grad, cfree=cfree.astype(bool), terms=terms, margin=margin)
+    if not states:
+        lib().cro_eval(C.byref(R), C.byref(W), _p(_f64(q_start)), _p(_f64(goal7)), _p(gq), C.byref(P),
+                       H, _p(th), B, _p(cost), _p(grad), _p(cfree, _up), _p(terms), _p(margin))
+        return dict(cost=cost, grad=grad, cfree=cfree.astype(bool), terms=terms, margin=margin)
+    st_terms = np.zeros((B, H, 2))
+    st_margin = np.zeros((B, H))
+    st_clear = np.zeros((B, H))
+    lib().cro_eval_states(C.byref(R), C.byref(W), _p(_f64(q_start)), _p(_f64(goal7)), _p(gq),
+                          C.byref(P), H, _p(th), B, _p(cost), _p(grad), _p(cfree, _up), _p(terms),
+                          _p(margin), _p(st_terms), _p(st_margin), _p(st_clear))
+    return dict(cost=cost, grad=grad, cfree=cfree.astype(bool), terms=terms, margin=margin,
+                state_terms=st_terms, state_margin=st_margin, state_clear=st_clear)
 
 
 class LbfgsState:

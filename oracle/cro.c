@@ -295,10 +295,17 @@ double cro_sweep_box(const double* pose7, const double* half_ext, double r, cons
     double dir[3] = {diff[0] / dist, diff[1] / dist, diff[2] / dist};
     double u = u0;
     for (int j = 0; j < steps; ++j) {
-      note_margin(margin, u - L);
-      if (u >= L) break;
       double p[3] = {x1[0] + u * dir[0], x1[1] + u * dir[1], x1[2] + u * dir[2]};
-      double pen = penetration(pose7, half_ext, r, p, gpen, margin);
+      double mface = DBL_MAX;
+      double pen = penetration(pose7, half_ext, r, p, gpen, &mface);
+      /* Margin bookkeeping only.  The stop test u >= L can change the result
+       * only when the sample at u is in collision: a sample out of collision
+       * adds nothing, and the next step (at least eta) passes L anyway.  So
+       * its distance from deciding anything is the larger of |u - L| and the
+       * sample's distance from the activation threshold. */
+      note_margin(margin, fmax(fabs(u - L), -eta - pen));
+      if (u >= L) break;
+      note_margin(margin, mface);
       note_margin(margin, pen + eta);
       if (pen > -eta) {
         S += cro_smooth_distance(pen, eta, &slope);
@@ -485,7 +492,8 @@ static void backward_state(const cro_robot* rb, const double* LT, const double* 
 static void eval_one(const cro_robot* rb, const box_t* boxes, int32_t K, const double* q_start,
                      const double* goal7, const double* goal_q, const cro_params* prm, int32_t H,
                      const double* theta,
-                     double* cost, double* grad, uint8_t* cfree, double* terms, double* margin) {
+                     double* cost, double* grad, uint8_t* cfree, double* terms, double* margin,
+                     double* st_terms, double* st_margin, double* st_clear) {
   const int D = rb->dof, M = rb->n_spheres;
   const int ik = (prm->flags & CRO_IK_MODE) != 0;
   const int swept = !ik && (prm->flags & CRO_SWEPT);
@@ -493,6 +501,13 @@ static void eval_one(const cro_robot* rb, const box_t* boxes, int32_t K, const d
   double term[CRO_N_TERMS] = {0, 0, 0, 0, 0};
   double mg = DBL_MAX;
   int free_ok = 1;
+  /* per-state bookkeeping (world and self cost of each state, the margin of
+   * the decisions that set its cost and gradient, its smallest clearance) */
+  double* sw = (double*)calloc((size_t)H, sizeof(double));
+  double* ss = (double*)calloc((size_t)H, sizeof(double));
+  double* smg = (double*)malloc((size_t)H * sizeof(double));
+  double* scl = (double*)malloc((size_t)H * sizeof(double));
+  for (int t = 0; t < H; ++t) smg[t] = scl[t] = DBL_MAX;
 
   /* forward kinematics of the start state (slot 0) and of theta_1..theta_H */
   double* LT = (double*)calloc((size_t)(H + 1) * D * 12, sizeof(double));
@@ -517,11 +532,11 @@ static void eval_one(const cro_robot* rb, const box_t* boxes, int32_t K, const d
       for (int k = 0; k < K; ++k) {
         double g1[3];
         Ssum += cro_sweep_box(boxes[k].pose, boxes[k].h, r, swept ? x0 : NULL, x1,
-                              swept ? x2 : NULL, prm->eta, prm->sweep_steps, g1, &mg);
+                              swept ? x2 : NULL, prm->eta, prm->sweep_steps, g1, &smg[t - 1]);
         for (int a = 0; a < 3; ++a) gS[a] += g1[a];
         /* validity flag: discrete clearance phi - r > 0 at every waypoint */
         double clear = cro_box_sdf(boxes[k].pose, boxes[k].h, x1, NULL) - r;
-        note_margin(&mg, clear);
+        if (clear < scl[t - 1]) scl[t - 1] = clear;
         if (!(clear > 0.0)) free_ok = 0;
       }
       double v = 1.0, dv[3] = {0, 0, 0};
@@ -533,6 +548,7 @@ static void eval_one(const cro_robot* rb, const box_t* boxes, int32_t K, const d
           for (int a = 0; a < 3; ++a) dv[a] = diff[a] / (n * 2.0 * prm->dt);
       }
       term[0] += prm->w_coll * v * Ssum;
+      sw[t - 1] += prm->w_coll * v * Ssum;
       double* gx1 = GX + ((size_t)t * M + i) * 3;
       for (int a = 0; a < 3; ++a) gx1[a] += prm->w_coll * v * gS[a];
       if (speed && Ssum != 0.0) {
@@ -556,17 +572,23 @@ static void eval_one(const cro_robot* rb, const box_t* boxes, int32_t K, const d
     const double* Xt = X + (size_t)t * M * 4;
     int32_t arg;
     double pen = cro_self_penetration(rb, Xt, &arg, gself);
-    if (pen > 0.0) note_margin(&mg, self_argmax_gap(rb, Xt));
+    /* the argmax pair decides the gradient */
+    if (pen > 0.0 && (prm->flags & CRO_SELF)) note_margin(&smg[t - 1], self_argmax_gap(rb, Xt));
     /* validity: every pair of S separated */
+    double pair_clear = DBL_MAX;
     for (int32_t p = 0; p < rb->n_pairs; ++p) {
       int i = rb->pairs[2 * p], j = rb->pairs[2 * p + 1];
       if (Xt[4 * i + 3] <= 0.0 || Xt[4 * j + 3] <= 0.0) continue;
       double d[3] = {Xt[4 * i] - Xt[4 * j], Xt[4 * i + 1] - Xt[4 * j + 1], Xt[4 * i + 2] - Xt[4 * j + 2]};
       double clear = norm3(d) - Xt[4 * i + 3] - Xt[4 * j + 3];
-      note_margin(&mg, clear);
+      if (clear < pair_clear) pair_clear = clear;
       if (!(clear > 0.0)) free_ok = 0;
     }
+    if (pair_clear < scl[t - 1]) scl[t - 1] = pair_clear;
+    /* max(0, .) of Eq. 9 switches the gradient on at zero penetration */
+    if (prm->flags & CRO_SELF) note_margin(&smg[t - 1], pair_clear);
     if (prm->flags & CRO_SELF) {
+      ss[t - 1] = prm->w_self * pen;
       term[1] += prm->w_self * pen;
       for (int k = 0; k < M * 3; ++k) GX[(size_t)t * M * 3 + k] += prm->w_self * gself[k];
     }
@@ -661,7 +683,20 @@ static void eval_one(const cro_robot* rb, const box_t* boxes, int32_t K, const d
   if (grad) memcpy(grad, G, (size_t)H * D * sizeof(double));
   if (cfree) *cfree = (uint8_t)free_ok;
   if (terms) memcpy(terms, term, sizeof(term));
+  /* the trajectory's margin: every decision of every state, clearances included */
+  for (int t = 0; t < H; ++t) {
+    note_margin(&mg, smg[t]);
+    note_margin(&mg, scl[t]);
+  }
   if (margin) *margin = mg;
+  if (st_terms)
+    for (int t = 0; t < H; ++t) {
+      st_terms[2 * t] = sw[t];
+      st_terms[2 * t + 1] = ss[t];
+    }
+  if (st_margin) memcpy(st_margin, smg, (size_t)H * sizeof(double));
+  if (st_clear) memcpy(st_clear, scl, (size_t)H * sizeof(double));
+  free(sw); free(ss); free(smg); free(scl);
   free(G); free(LT); free(X); free(GX);
 }
 
@@ -669,6 +704,15 @@ void cro_eval(const cro_robot* rb, const cro_world* w, const double* q_start, co
               const double* goal_q, const cro_params* prm, int32_t H, const double* theta, int32_t B,
               double* cost,
               double* grad, uint8_t* cfree, double* terms, double* margin) {
+  cro_eval_states(rb, w, q_start, goal7, goal_q, prm, H, theta, B, cost, grad, cfree, terms, margin,
+                  NULL, NULL, NULL);
+}
+
+void cro_eval_states(const cro_robot* rb, const cro_world* w, const double* q_start,
+                     const double* goal7, const double* goal_q, const cro_params* prm, int32_t H,
+                     const double* theta, int32_t B, double* cost, double* grad, uint8_t* cfree,
+                     double* terms, double* margin, double* state_terms, double* state_margin,
+                     double* state_clear) {
   box_t* boxes = (box_t*)malloc((size_t)(w->n > 0 ? w->n : 1) * sizeof(box_t));
   for (int k = 0; k < w->n; ++k) {
     memcpy(boxes[k].pose, w->pose + 7 * k, 7 * sizeof(double));
@@ -678,7 +722,10 @@ void cro_eval(const cro_robot* rb, const cro_world* w, const double* q_start, co
   for (int b = 0; b < B; ++b) {
     eval_one(rb, boxes, w->n, q_start, goal7, goal_q, prm, H, theta + b * n, cost + b,
              grad ? grad + b * n : NULL, cfree ? cfree + b : NULL,
-             terms ? terms + (size_t)b * CRO_N_TERMS : NULL, margin ? margin + b : NULL);
+             terms ? terms + (size_t)b * CRO_N_TERMS : NULL, margin ? margin + b : NULL,
+             state_terms ? state_terms + (size_t)b * H * 2 : NULL,
+             state_margin ? state_margin + (size_t)b * H : NULL,
+             state_clear ? state_clear + (size_t)b * H : NULL);
   }
   free(boxes);
 }

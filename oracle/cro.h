@@ -139,6 +139,24 @@ void cro_eval(const cro_robot* rb, const cro_world* w, const double* q_start, co
               const cro_params* prm, int32_t H, const double* theta, int32_t B, double* cost,
               double* grad, uint8_t* cfree, double* terms, double* margin);
 
+/* cro_eval with per-state outputs, for parity checks that skip single
+ * states instead of whole trajectories (any output may be NULL):
+ *   state_terms  [B][H][2]: the world cost (Eq. 11, summed over spheres) and
+ *                the self cost (Eq. 9, weighted) of each state theta_t;
+ *   state_margin [B][H]: the smallest distance from its threshold of any
+ *                decision that sets that state's world or self cost or its
+ *                gradient (sweep activation and stop tests, face and pair
+ *                argmax, the zero of max(0, .) in Eq. 9); a decision of state
+ *                t reaches the gradient rows t-1, t, t+1 (speed metric);
+ *   state_clear  [B][H]: the smallest discrete clearance of the state (every
+ *                sphere against every box, every pair of S unless the self
+ *                check is off); the state is collision-free when it is > 0. */
+void cro_eval_states(const cro_robot* rb, const cro_world* w, const double* q_start,
+                     const double* goal7, const double* goal_q, const cro_params* prm, int32_t H,
+                     const double* theta, int32_t B, double* cost, double* grad, uint8_t* cfree,
+                     double* terms, double* margin, double* state_terms, double* state_margin,
+                     double* state_clear);
+
 /* ---- optimiser (Sec. 4.1, Alg. 1, App. A.7 L-BFGS step update) ----------- */
 
 /* Per-seed optimiser state.  All arrays are caller-owned. */

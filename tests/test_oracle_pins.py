@@ -452,6 +452,123 @@ def test_sweep_gradient_equals_rigid_translation_derivative(oracle_mod):
         assert (Sp - Sm) / 2e-6 == pytest.approx(g[a], rel=1e-6, abs=1e-8)
 
 
+def test_sweep_stop_margin_counts_only_reachable_samples(oracle_mod):
+    """The stop test u >= L of the march is a decision that matters only when
+    the sample at u would be in collision.  Toward a face with the first step
+    landing exactly at the midpoint, the sample would touch the box: moving the
+    neighbour by 1e-9 adds or drops a term of eta / 2, and the margin is ~0.
+    Away from the box the same stop test can change nothing and sets no small
+    margin."""
+    eta, r, d = 0.025, 0.05, 0.1
+    pose = np.array([0.0, 0, 0, 1, 0, 0, 0])
+    he = np.array([0.5, 0.5, 0.5])
+    x1 = np.array([-0.5 - r - d, 0, 0])          # phi - r = d: first step u0 = d
+    toward = x1 + np.array([2 * d, 0, 0])       # midpoint L = d: stop exactly at u0
+    S0, _, m0 = oracle_mod.sweep_box(pose, he, r, None, x1, toward, eta, 4)
+    Sp, _, _ = oracle_mod.sweep_box(pose, he, r, None, x1, toward + [1e-9, 0, 0], eta, 4)
+    assert m0 < 1e-12
+    assert S0 == 0.0 and Sp == pytest.approx(0.5 * eta, abs=1e-8)   # the sample touches: pen = 0
+    away = x1 - np.array([2 * d, 0, 0])
+    S1, _, m1 = oracle_mod.sweep_box(pose, he, r, None, x1, away, eta, 4)
+    S2, _, _ = oracle_mod.sweep_box(pose, he, r, None, x1, away - [1e-9, 0, 0], eta, 4)
+    assert S1 == 0.0 and S2 == 0.0
+    # the waypoint's activation test is the closest decision: |(r - phi) + eta| = d - eta
+    assert m1 == pytest.approx(d - eta, abs=1e-12)
+
+
+def _state_scene(oracle_mod, seed=6):
+    """42 spheres, 6 boxes near the arm, 3 trajectories of 7 states with the
+    joints pushed toward their limits (the chain folds onto itself)."""
+    rb = _robot()
+    rng = np.random.default_rng(seed)
+    K = 6
+    w = synth.World(pose=np.array([[*rng.uniform(-0.4, 0.4, 3), *_quat_axis_angle(rng.normal(size=3), 0.5)]
+                                   for _ in range(K)]), half_ext=rng.uniform(0.05, 0.15, (K, 3)))
+    lo, hi = np.asarray(rb.q_lo), np.asarray(rb.q_hi)
+    u = rng.uniform(0.0, 1.0, (3, 7, rb.dof)) ** 0.25 * np.where(rng.uniform(size=(3, 7, rb.dof)) < 0.5, -1, 1)
+    th = 0.5 * (lo + hi) + 0.45 * (hi - lo) * u
+    qs = th[0, 0]
+    goal = oracle_mod.goal_pose_from_fk(rb, th[0, -1])
+    return rb, w, qs, goal, th
+
+
+def test_state_outputs_brute_force(oracle_mod):
+    """Per-state outputs of the evaluation against a recomputation from the
+    pinned pieces (kinematics, sweep, self term, box distance): the world cost
+    of state t is beta_2 sum_i v_i,t sum_k S_ik with the neighbours t - 1 and
+    t + 1 of the padded sequence, the self cost beta_1 times the deepest pair,
+    the clearance the smallest of every sphere-box and pair clearance; they add
+    up to the trajectory's terms and decide its flag."""
+    rb, w, qs, goal, th = _state_scene(oracle_mod)
+    p = oracle_mod.params_default()
+    out = oracle_mod.evaluate(rb, w, qs, goal, th, states=True)
+    B, H, _ = th.shape
+    M = len(rb.spheres)
+    assert (out["state_terms"][:, :, 0] > 0).any() and (out["state_terms"][:, :, 1] > 0).any()
+    for b in range(B):
+        X = [oracle_mod.fk(rb, qs)[1]] + [oracle_mod.fk(rb, th[b, t])[1] for t in range(H)]
+        for t in range(1, H + 1):
+            tp = min(t + 1, H)
+            world, clear = 0.0, np.inf
+            for i in range(M):
+                x0, x1, x2 = X[t - 1][i, :3], X[t][i, :3], X[tp][i, :3]
+                r = X[t][i, 3]
+                S = sum(oracle_mod.sweep_box(w.pose[k], w.half_ext[k], r, x0, x1, x2, p["eta"],
+                                             p["sweep_steps"])[0] for k in range(len(w.pose)))
+                v = np.linalg.norm(x2 - x0) / (2 * p["dt"])
+                world += p["w_coll"] * v * S
+                for k in range(len(w.pose)):
+                    clear = min(clear, oracle_mod.box_sdf(w.pose[k], w.half_ext[k], x1)[0] - r)
+            pen, _, _ = oracle_mod.self_penetration(rb, X[t])
+            for i, j in rb.pairs:
+                clear = min(clear, np.linalg.norm(X[t][i, :3] - X[t][j, :3]) - X[t][i, 3] - X[t][j, 3])
+            assert out["state_terms"][b, t - 1, 0] == pytest.approx(world, rel=1e-12, abs=1e-12)
+            assert out["state_terms"][b, t - 1, 1] == pytest.approx(p["w_self"] * pen, rel=1e-12, abs=1e-12)
+            assert out["state_clear"][b, t - 1] == pytest.approx(clear, rel=1e-12, abs=1e-14)
+    np.testing.assert_allclose(out["state_terms"].sum(1), out["terms"][:, :2], rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(out["cfree"], (out["state_clear"] > 0).all(1))
+    mg = np.minimum(out["state_margin"].min(1), np.abs(out["state_clear"]).min(1))
+    np.testing.assert_allclose(out["margin"], mg, rtol=0, atol=0)
+
+
+def test_state_margin_marks_self_argmax_tie(oracle_mod):
+    """Two sphere pairs that penetrate equally at one state put that state's
+    margin at zero (the gradient may go to either pair); the other states keep
+    a margin away from zero.  Chain of three z joints one metre apart; folding
+    joint 1 by pi brings link 2's frame back to the origin, turned by pi, so
+    link 2's spheres (-0.625, 0) and (-0.625, -0.5) land 0.125 from link 0's
+    spheres (0.5, 0) and (0.5, 0.5)."""
+    ident = np.eye(3, 4).reshape(12)
+    fixed = np.stack([ident] * 4)
+    fixed[1, 3] = 1.0                              # F_1, F_2: one metre along x
+    fixed[2, 3] = 1.0
+    rb = synth.Robot(fixed_tf=fixed, axis=np.array([2, 2, 2], np.int32), q_lo=-4 * np.ones(3),
+                     q_hi=4 * np.ones(3), v_max=np.ones(3), a_max=np.ones(3), j_max=np.ones(3),
+                     spheres=np.array([[0.5, 0.0, 0, 0.1], [0.5, 0.5, 0, 0.1],
+                                       [-0.625, 0.0, 0, 0.1], [-0.625, -0.5, 0, 0.1]]),
+                     sphere_link=np.array([0, 0, 2, 2], np.int32), pairs=np.array([[0, 2], [1, 3]], np.int32))
+    w = synth.World(pose=np.zeros((0, 7)), half_ext=np.zeros((0, 3)))
+    q_fold = np.array([0.0, math.pi, 0.0])
+    _, sp, _ = oracle_mod.fk(rb, q_fold)
+    d0 = np.linalg.norm(sp[0, :3] - sp[2, :3])
+    d1 = np.linalg.norm(sp[1, :3] - sp[3, :3])
+    assert d0 == pytest.approx(0.125, abs=1e-14) and d1 == pytest.approx(0.125, abs=1e-14)
+    th = np.zeros((2, 3, 3))
+    th[0, 1] = q_fold
+    out = oracle_mod.evaluate(rb, w, np.zeros(3), np.array([0, 0, 1.0, 1, 0, 0, 0]), th,
+                              dict(flags=oracle_mod.SELF | oracle_mod.SPEED | oracle_mod.SWEPT),
+                              states=True)
+    assert out["state_terms"][0, 1, 1] == pytest.approx(5000 * 0.075, rel=1e-12)
+    assert out["state_margin"][0, 1] < 1e-12
+    assert out["state_margin"][0, 0] > 0.1 and out["state_margin"][0, 2] > 0.1
+    assert (out["state_margin"][1] > 0.1).all()
+    # without the self term the tie decides nothing; the clearance still flags the contact
+    out = oracle_mod.evaluate(rb, w, np.zeros(3), np.array([0, 0, 1.0, 1, 0, 0, 0]), th,
+                              dict(flags=oracle_mod.SPEED | oracle_mod.SWEPT), states=True)
+    assert (out["state_margin"] > 0.1).all()
+    assert out["state_clear"][0, 1] == pytest.approx(-0.075, abs=1e-14) and not out["cfree"][0]
+
+
 # ---------------------------------------------------------------------------
 # Eq. 14 pose cost
 # ---------------------------------------------------------------------------
