@@ -168,12 +168,16 @@ cr_status cr_fk(const cr_robot* robot, const float* theta, int32_t n, float* sph
  *   cfree  device [B] uint8: 1 when every waypoint is clear of every box and
  *          every pair of S is separated (discrete check), or NULL
  *   terms  device [B][5] world, self, bound, smoothness, goal, or NULL
+ *   state_terms  device [B][H][2] the world cost (Eq. 11 summed over the
+ *          spheres) and the self cost (Eq. 9, weighted) of every state, or
+ *          NULL; they add up to terms[0] and terms[1] (up to FP32 rounding
+ *          order)
  * One fused kernel launch; link transforms stay on chip between the forward
  * and backward passes.  Deterministic: a trajectory's results do not depend
  * on B or on the other trajectories. */
 cr_status cr_eval(const cr_robot* robot, const cr_problem* problem, const cr_params* params,
                   const float* theta, int32_t B, float* cost, float* grad, uint8_t* cfree,
-                  float* terms, void* stream);
+                  float* terms, float* state_terms, void* stream);
 
 /* Device-resident optimiser state of B seeds with n = H*dof variables each
  * (Sec. 4.1, App. A.7).  Every pointer is device memory owned by the caller.
@@ -413,11 +417,14 @@ cr_status cr_server_stats(cr_server* server, int32_t* active, int32_t* queued, s
  * At most CR_NOALLOC_MAX_PROBLEMS problems and CR_NOALLOC_MAX_TILES tiles (one
  * tile per trajectory when H >= 32, ceil(32/H) trajectories per tile below);
  * larger batches return CR_EINVAL.  The first call on a device looks up the
- * array's device address (a one-time set-up with that device current); make
- * that first call before any stream capture.  Every call shares the one
- * array, so calls whose work overlaps on the GPU (different streams, or
+ * array's device address (a one-time set-up with that device current).  The
+ * problem and tile tables are staged from host memory that exists only during
+ * the call, with cudaMemcpyAsync from pageable memory: the call may block the
+ * host until `stream` reaches those copies, and while `stream` is being
+ * captured it returns CR_EINVAL and enqueues nothing.  Every call shares the
+ * one array, so calls whose work overlaps on the GPU (different streams, or
  * different host threads) race: order them on one stream.  Results equal
- * those of cr_eval on each problem. */
+ * those of cr_eval on each problem, bit for bit. */
 cr_status cr_eval_batch_noalloc(const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
                                 const cr_params* params, const int32_t* n_traj, const float* theta,
                                 float* cost, float* grad, uint8_t* cfree, float* terms, void* stream);

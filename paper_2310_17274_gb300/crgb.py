@@ -86,7 +86,7 @@ SIGNATURES = {
     "cr_world_destroy": ([_vp], None),
     "cr_fk": ([_vp, _vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int32),
     "cr_eval": ([_vp, C.POINTER(Problem), C.POINTER(Params), _vp, C.c_int32, _vp, _vp, _vp, _vp,
-                 _vp], C.c_int32),
+                 _vp, _vp], C.c_int32),
     "cr_opt_propose": ([_vp, C.POINTER(Params), C.POINTER(OptState), _vp], C.c_int32),
     "cr_opt_select": ([_vp, C.POINTER(Params), C.POINTER(OptState), _vp], C.c_int32),
     "cr_context_create": ([C.c_int, C.c_size_t, C.POINTER(_vp)], C.c_int32),
@@ -288,9 +288,10 @@ def fk(robot: Robot, theta, spheres=True, ee=True, link_tf=False, stream=None):
 
 
 def evaluate(robot: Robot, problem: ProblemSpec, theta, params=None, want_grad=True,
-             want_terms=True, stream=None):
+             want_terms=True, want_states=False, stream=None):
     """Cost, gradient, collision-free flags and per-term costs of theta
-    (CUDA float32 tensor [B, H, dof]) in one fused launch."""
+    (CUDA float32 tensor [B, H, dof]) in one fused launch; with want_states
+    also the world and self cost of every state ([B, H, 2])."""
     import torch
     theta = theta.contiguous()
     B = theta.shape[0]
@@ -299,11 +300,13 @@ def evaluate(robot: Robot, problem: ProblemSpec, theta, params=None, want_grad=T
     grad = torch.empty_like(theta) if want_grad else None
     cfree = torch.empty(B, device=dev, dtype=torch.uint8)
     terms = torch.empty((B, N_TERMS), device=dev) if want_terms else None
+    states = torch.empty((B, theta.shape[1], 2), device=dev) if want_states else None
     P = params if isinstance(params, Params) else make_params(params)
     pr = problem.struct()
     check(lib().cr_eval(robot.handle, C.byref(pr), C.byref(P), _dptr(theta), B, _dptr(cost),
-                        _dptr(grad), _dptr(cfree), _dptr(terms), _stream(stream)), "cr_eval")
-    return dict(cost=cost, grad=grad, cfree=cfree, terms=terms)
+                        _dptr(grad), _dptr(cfree), _dptr(terms), _dptr(states), _stream(stream)),
+          "cr_eval")
+    return dict(cost=cost, grad=grad, cfree=cfree, terms=terms, state_terms=states)
 
 
 def particle_step(robot: Robot, problem: ProblemSpec, mu, sigma, eps, params=None, beta=1.0,

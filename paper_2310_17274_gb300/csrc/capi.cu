@@ -373,7 +373,7 @@ cr_status cr_fk(const cr_robot* robot, const float* theta, int32_t n, float* sph
 
 cr_status cr_eval(const cr_robot* robot, const cr_problem* problem, const cr_params* params,
                   const float* theta, int32_t B, float* cost, float* grad, uint8_t* cfree,
-                  float* terms, void* stream) {
+                  float* terms, float* state_terms, void* stream) {
   if (!robot) return fail(CR_EINVAL, "cr_eval: null robot");
   cr_status s = check_params(params);
   if (s != CR_OK) return s;
@@ -399,6 +399,7 @@ cr_status cr_eval(const cr_robot* robot, const cr_problem* problem, const cr_par
   a.grad = grad;
   a.cfree = cfree;
   a.terms = terms;
+  a.state_terms = state_terms;
   a.no_store_x = -1;
   const int block = kEvalBlock;
   const int smem = eval_smem_bytes(a, block);

@@ -111,6 +111,7 @@ struct EvalArgs {
   float* grad;
   uint8_t* cfree;
   float* terms;
+  float* state_terms;            // [states][2] world and self cost of each state, or nullptr
 };
 
 // Shared-memory carve-up of the evaluation kernel (host and device agree).

@@ -812,6 +812,11 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
       if (a.grad) a.grad[vbase + k] = g;
     }
 
+    // per-state world and self costs (optional output)
+    if (a.state_terms) {
+      float2* out = reinterpret_cast<float2*>(a.state_terms) + vbase / D;
+      for (int k = tid; k < S; k += nthr) out[k] = make_float2(s_stw[k], selfc ? prm.w_self * s_sts[k] : 0.f);
+    }
     // ---- per-trajectory cost in a fixed order
     for (int r = warp; r < nt; r += nw) {
       float tw = 0.f, ts = 0.f, tb = 0.f, tsm = 0.f;

@@ -281,6 +281,7 @@ __global__ void __launch_bounds__(NT, NT == kIkThreadsGrad ? 5 : 1) k_eval_ik(co
       // has both), else every listed pair of the link pair.  The deepest
       // penetration wins, the first pair of the caller's list on exact ties;
       // every listed pair counts for the collision-free flag.
+      float tss = 0.f;  // the state's self cost
       if (P > 0 && !(flags & CR_NO_SELF_CHECK)) {
         float best = 0.f;
         int arg = -1;
@@ -391,7 +392,8 @@ __global__ void __launch_bounds__(NT, NT == kIkThreadsGrad ? 5 : 1) k_eval_ik(co
           }
         }
         if (selfc) {
-          ts += prm.w_self * best;
+          tss = prm.w_self * best;
+          ts += tss;
           if (GRAD && arg >= 0 && sub == 0) {
             const uint32_t pr = __ldg(&a.rb.pairs[arg]);
             const int pi = (int)(pr & 0xffffu), pj = (int)(pr >> 16);
@@ -417,6 +419,8 @@ __global__ void __launch_bounds__(NT, NT == kIkThreadsGrad ? 5 : 1) k_eval_ik(co
       }
       if (TPT > 1) free_ok = __all_sync(gmask, free_ok);
       if (sub != 0) continue;  // the rest of the state: one thread
+      if (a.state_terms)
+        reinterpret_cast<float2*>(a.state_terms)[vb / D + t] = make_float2(tws, tss);
 
       // ---- Eq. 14 pose goal and Eq. 15 joint-space goal at the last state
       if (t == H - 1) {

@@ -91,7 +91,7 @@ extern "C" cr_status cr_particle_step(const cr_robot* robot, const cr_problem* p
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(CR_ECUDA, cudaGetErrorString(e));
   cr_status st = cr_eval(robot, problem, params, particles, n_seeds * n_particles, cost, nullptr,
-                         nullptr, nullptr, stream);
+                         nullptr, nullptr, nullptr, stream);
   if (st != CR_OK) return st;
   k_particle_update<<<n_seeds, 256, (size_t)n_particles * sizeof(float), s>>>(
       cost, particles, mu, sigma, n, n_particles, 1.f / beta, k_mu, k_sigma);

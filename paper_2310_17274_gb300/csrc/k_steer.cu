@@ -85,7 +85,7 @@ extern "C" cr_status cr_steer(const cr_robot* robot, const cr_world* world, int3
   pr.q_start = q0;
   pr.goal = goal;
   pr.horizon = 1;
-  cr_status st = cr_eval(robot, &pr, &prm, samples, n_edges * (n + 1), cost, nullptr, valid, nullptr, stream);
+  cr_status st = cr_eval(robot, &pr, &prm, samples, n_edges * (n + 1), cost, nullptr, valid, nullptr, nullptr, stream);
   if (st != CR_OK) return st;
   k_steer_reduce<<<(n_edges + 127) / 128, 128, 0, s>>>(edges, valid, n_edges, n, D, last, v_new, dist);
   e = cudaGetLastError();

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <vector>
 
@@ -40,7 +41,10 @@ constexpr size_t kScratchBytes = kQueueOff + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
+// device address of the scratch array per device, looked up once; host
+// threads making their first call on a device at the same time each store the
+// same address
+std::atomic<unsigned char*> g_scratch_addr[kMaxDevices] = {};
 
 cr_status fail(cr_status code, const char* msg) { return set_error(code, msg); }
 
@@ -61,15 +65,27 @@ extern "C" cr_status cr_eval_batch_noalloc(const cr_robot* robot, int32_t n_prob
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(CR_ECUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(CR_EINVAL, "cr_eval_batch_noalloc: device index >= 64");
-  if (!g_scratch_addr[dev]) {
+  cudaStream_t st = (cudaStream_t)stream;
+  {
+    // the tables below are copied from host memory that lives only during
+    // this call: a captured copy would read it after it is gone
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return fail(CR_ECUDA, cudaGetErrorString(e));
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(CR_EINVAL, "cr_eval_batch_noalloc: the stream is being captured (the call stages its "
+                             "tables from temporary host memory and cannot be recorded)");
+  }
+  unsigned char* scratch = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!scratch) {
     // once per device, with that device current: the device address of the
     // scratch array (its host-side name is only a stand-in)
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return fail(CR_ECUDA, cudaGetErrorString(e));
-    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+    scratch = static_cast<unsigned char*>(p);
+    g_scratch_addr[dev].store(scratch, std::memory_order_release);
   }
-  unsigned char* scratch = g_scratch_addr[dev];
 
   std::vector<ProblemView> pv(n_problems);
   std::vector<int4> tiles;
@@ -99,7 +115,6 @@ extern "C" cr_status cr_eval_batch_noalloc(const cr_robot* robot, int32_t n_prob
   if (tiles.empty()) return CR_OK;
   if (!theta || !cost) return fail(CR_EINVAL, "cr_eval_batch_noalloc: null theta or cost");
 
-  cudaStream_t st = (cudaStream_t)stream;
   e = cudaMemcpyAsync(scratch, pv.data(), pv.size() * sizeof(ProblemView), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(scratch + kTileOff, tiles.data(), tiles.size() * sizeof(int4),

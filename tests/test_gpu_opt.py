@@ -98,14 +98,29 @@ def test_propose_matches_oracle(H, m, k_steps):
         assert int(buf.iter[b]) == int(st.iter[0])
 
 
-def test_select_matches_oracle_on_real_problem():
+_EVAL_FLAGS = crgb.SWEPT | crgb.SPEED | crgb.SELF
+
+# line-search variants of Sec. 7.3: (step sizes, selection flags, seeds that must
+# be decided away from every threshold)
+LS_VARIANTS = {
+    "noisy-ls": ([0.01, 0.3, 0.7, 1.0], crgb.WOLFE, 4),
+    "noisy-ls-1": ([0.01, 1.0], crgb.WOLFE, 4),
+    "strong-wolfe": ([0.01, 0.3, 0.7, 1.0], crgb.WOLFE | crgb.STRONG_WOLFE, 3),
+    "armijo-only": ([0.01, 0.3, 0.7, 1.0], 0, 4),
+    "no-ls": ([1.0], 0, 6),
+}
+
+
+@pytest.mark.parametrize("variant", list(LS_VARIANTS))
+def test_select_matches_oracle_on_real_problem(variant):
     """Propose from evaluated seeds, evaluate the candidates with the oracle,
-    then select on both sides."""
+    then select on both sides, for each line-search variant of Sec. 7.3."""
     rb, w, pr = scene(n_seeds=6, horizon=32)
     D, H, B = rb.dof, 32, 6
     n = H * D
-    p = dict(alpha=[0.01, 0.3, 0.7, 1.0])
-    na = 4
+    alphas, ls_flags, min_strict = LS_VARIANTS[variant]
+    p = dict(alpha=alphas, flags=_EVAL_FLAGS | ls_flags)
+    na = len(alphas)
     ev0 = oracle.evaluate(rb, w, pr.q_start, pr.goal, pr.seeds)
     buf = crgb.OptBuffers(B, H, D, 6, na, device="cuda")
     buf.x.copy_(torch.tensor(pr.seeds.reshape(B, n), dtype=torch.float32))
@@ -139,7 +154,45 @@ def test_select_matches_oracle_on_real_problem():
         assert float(buf.c[b]) == np.float32(cc[b, k])
         assert float(buf.best_c[b]) == np.float32(cc[b, k])  # best was +inf
         np.testing.assert_array_equal(buf.best_x[b].cpu().numpy(), cand[b, k].astype(np.float32))
-    assert n_strict >= 4
+    assert n_strict >= min_strict
+
+
+def test_weak_and_strong_wolfe_choose_differently():
+    """Directional derivatives g_l . d of -0.95, -0.5, +0.5 and +0.95 times
+    |g_0 . d| with every candidate below the Armijo line: the weak Wolfe test
+    (g_l . d >= 0.9 g_0 . d) passes steps 1-3 and takes 3, the strong one
+    (|g_l . d| <= 0.9 |g_0 . d|) passes 1-2 and takes 2, Armijo alone takes 3;
+    the oracle agrees on each."""
+    rb, _, _ = scene()
+    D, H, na = rb.dof, 2, 4
+    n = H * D
+    R = crgb.Robot(rb)
+    g0 = np.zeros(n, np.float32)
+    g0[0] = 1.0                                   # g_0 . d = -1 with d = -g_0
+    d = -g0
+    slopes = np.array([-0.95, -0.5, 0.5, 0.95], np.float32)
+    cgrad = np.zeros((na, n), np.float32)
+    cgrad[:, 0] = -slopes                         # g_l . d = slopes[l]
+    cost = np.full(na, 0.5, np.float32)           # c_0 = 1: Armijo holds for every step
+    expect = {crgb.WOLFE: 3, crgb.WOLFE | crgb.STRONG_WOLFE: 2, 0: 3}
+    for fl, want in expect.items():
+        p = dict(alpha=[0.1, 0.3, 0.7, 1.0], flags=_EVAL_FLAGS | fl)
+        buf = crgb.OptBuffers(1, H, D, 2, na, device="cuda")
+        buf.x.zero_()
+        buf.g.copy_(torch.tensor(g0)[None])
+        buf.dir.copy_(torch.tensor(d)[None])
+        buf.c.fill_(1.0)
+        buf.best_c.fill_(float("inf"))
+        buf.cand.copy_(torch.arange(na, dtype=torch.float32).view(1, na, 1).expand(1, na, n))
+        buf.cand_cost.copy_(torch.tensor(cost)[None])
+        buf.cand_grad.copy_(torch.tensor(cgrad)[None])
+        buf.cand_cfree.fill_(1)
+        crgb.opt_select(R, p, buf)
+        torch.cuda.synchronize()
+        idx, _ = oracle.ls_select(p, 1.0, g0, d, cost, cgrad)
+        assert idx == want, (fl, idx)
+        assert int(buf.ls_index[0]) == want, (fl, int(buf.ls_index[0]))
+        assert float(buf.x[0, 0]) == float(want)
 
 
 def test_select_fallback_and_best_tracking():

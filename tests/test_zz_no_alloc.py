@@ -7,9 +7,11 @@ application whose own pool owns all device memory.  Its scratch lives in a
 fixed device array inside the library; the caller passes inputs and outputs.
 
 Checked here through the C ABI: two calls in a row give what the regular
-per-problem entry point (cr_eval) gives, within the parity tests' tolerance,
-and batches beyond the stated maximum are refused with a clear error.
-This file is collected last on purpose.
+per-problem entry point (cr_eval) gives, bit for bit (trajectory problems and
+IK-mode problems of uneven trajectory counts), batches beyond the stated
+maximum are refused with a clear error, and a call on a stream that is being
+captured is refused before it enqueues anything.  This file is collected last
+on purpose.
 """
 import numpy as np
 import pytest
@@ -41,9 +43,10 @@ def setup():
     return R, cases
 
 
-def _close(a, b):
-    a, b = a.cpu().numpy(), b.cpu().numpy()
-    return np.allclose(a, b, rtol=1e-5, atol=1e-6)
+def _same(ref, out, call):
+    for r, o in zip(ref, out):
+        for k in ("cost", "grad", "terms", "cfree"):
+            assert torch.equal(o[k], r[k]), (call, k)
 
 
 def test_noalloc_matches_regular_entry_point_twice(setup):
@@ -52,11 +55,47 @@ def test_noalloc_matches_regular_entry_point_twice(setup):
     for call in range(2):
         out = crgb.evaluate_batch_noalloc(R, [c[1] for c in cases], [c[2] for c in cases])
         torch.cuda.synchronize()
-        for r, o in zip(ref, out):
-            assert _close(o["cost"], r["cost"]), call
-            assert _close(o["grad"], r["grad"]), call
-            assert _close(o["terms"], r["terms"]), call
-            assert torch.equal(o["cfree"], r["cfree"]), call
+        _same(ref, out, call)
+
+
+def test_noalloc_ik_mode_uneven_problems_twice(setup):
+    """IK mode (single states on their own kernel): problems of 1, 37, 64 and
+    300 configurations with different worlds in one call."""
+    R, _ = setup
+    rb = scene(spheres=synth.SPHERES_60)[0]
+    specs, thetas = [], []
+    rng = np.random.default_rng(50)
+    for k, (K, n) in enumerate([(0, 1), (40, 37), (12, 64), (70, 300)]):
+        _, w, pr = scene(spheres=synth.SPHERES_60, n_boxes=K, n_seeds=1, horizon=1, world_seed=60 + k,
+                         problem_seed=70 + k)
+        W = crgb.World(w)
+        specs.append((W, crgb.ProblemSpec(W, pr.q_start, pr.goal, 1)))
+        q = synth.uniform_config(rng, rb, n)[:, None, :]
+        thetas.append(torch.tensor(q, dtype=torch.float32, device="cuda"))
+    p = dict(flags=crgb.IK_MODE | crgb.SELF)
+    ref = [crgb.evaluate(R, sp, th, p) for (_, sp), th in zip(specs, thetas)]
+    for call in range(2):
+        out = crgb.evaluate_batch_noalloc(R, [sp for _, sp in specs], thetas, p)
+        torch.cuda.synchronize()
+        _same(ref, out, call)
+    assert 0 < int(sum(int(r["cfree"].sum()) for r in ref)) < 402
+
+
+def test_noalloc_refuses_a_capturing_stream(setup):
+    R, cases = setup
+    _, spec, th = cases[0]
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with pytest.raises(crgb.CrError, match="captured"):
+        with torch.cuda.graph(g, stream=s):
+            crgb.evaluate_batch_noalloc(R, [spec], [th])
+    torch.cuda.synchronize()
+    # the library is usable afterwards
+    out = crgb.evaluate_batch_noalloc(R, [spec], [th])
+    ref = crgb.evaluate(R, spec, th)
+    torch.cuda.synchronize()
+    _same([ref], out, 0)
 
 
 def test_noalloc_refuses_oversized_batches(setup):
