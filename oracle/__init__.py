@@ -111,6 +111,12 @@ def lib():
         L.cro_eval_states.argtypes = [C.POINTER(_Robot), C.POINTER(_World), _dp, _dp, _dp,
                                       C.POINTER(_Params), C.c_int32, _dp, C.c_int32, _dp, _dp, _up,
                                       _dp, _dp, _dp, _dp, _dp]
+        L.cro_time_scaled_params.argtypes = [C.POINTER(_Params), C.c_double, C.c_int32, C.POINTER(_Params)]
+        L.cro_time_discretized_solve.argtypes = [C.POINTER(_Robot), C.POINTER(_World), _dp, _dp, _dp,
+                                                 C.POINTER(_Params), C.c_int32, C.c_int32, _dp, C.c_int32,
+                                                 C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double,
+                                                 C.c_double, _dp, _dp, _dp, _dp, _up, _dp, _dp]
+        L.cro_time_discretized_solve.restype = C.c_int32
         L.cro_lbfgs_direction.argtypes = [C.POINTER(_Lbfgs), _dp]
         L.cro_ls_candidates.argtypes = [C.POINTER(_Params), C.c_int32, C.c_int32, _dp, _dp,
                                         _dp, _dp, _dp]
@@ -527,3 +533,37 @@ def retime(rb, q0, theta):
     R = _robot(rb, keep)
     th = _f64(theta)
     return float(lib().cro_retime(C.byref(R), th.shape[0], _p(_f64(q0)), _p(th)))
+
+
+def time_scaled_params(params, dt, jerk=True) -> dict:
+    """cro_time_scaled_params: the parameters for step dt (weights on the k-th
+    derivative's square times (dt / dt0)^(2k); jerk=False zeroes the jerk weight)."""
+    P = _params(params)
+    out = _Params()
+    lib().cro_time_scaled_params(C.byref(P), float(dt), int(bool(jerk)), C.byref(out))
+    return _params_to_dict(out)
+
+
+def time_discretized_solve(rb, world, q_start, goal7, seeds, iters1, iters2, params=None, dt_init=0.25,
+                           dt_min=1e-3, w_pose=1.0, w_jerk=1e-3, w_time=1.0, goal_q=None):
+    """Alg. "Time Discretization" (cro_time_discretized_solve) for one problem."""
+    keep = _Keep()
+    R = _robot(rb, keep)
+    W = _world(world, keep)
+    P = _params(params)
+    sd = _f64(seeds)
+    B, H, dof = sd.shape
+    first = np.zeros((H, dof))
+    stage = np.zeros(8)
+    traj = np.zeros_like(sd)
+    cost = np.zeros(B)
+    cfree = np.zeros(B, dtype=np.uint8)
+    dt = np.zeros(B)
+    score = np.zeros(B)
+    gq = None if goal_q is None else _f64(goal_q)
+    chosen = lib().cro_time_discretized_solve(
+        C.byref(R), C.byref(W), _p(_f64(q_start)), _p(_f64(goal7)), _p(gq), C.byref(P), H, B, _p(sd),
+        int(iters1), int(iters2), float(dt_init), float(dt_min), float(w_pose), float(w_jerk), float(w_time),
+        _p(first), _p(stage), _p(traj), _p(cost), _p(cfree, _up), _p(dt), _p(score))
+    return dict(first=first, stage=stage, traj=traj, cost=cost, cfree=cfree.astype(bool), dt=dt, score=score,
+                chosen=int(chosen))

@@ -1054,3 +1054,64 @@ int32_t cro_rank_seeds(const cro_robot* rb, int32_t H, int32_t B, const double* 
   free(v); free(a); free(j);
   return best;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Alg. "Time Discretization" (App. "Time-step Discretization")               */
+/* ------------------------------------------------------------------------ */
+
+/* Reading of "scale the weights by the new dt": the App. A.5 derivatives of
+ * the same waypoints scale as 1/dt^k, so multiplying the weight on the square
+ * of the k-th derivative by (dt / dt0)^(2k) keeps the term's value. */
+void cro_time_scaled_params(const cro_params* prm, double dt, int32_t jerk, cro_params* out) {
+  double r = dt / prm->dt;
+  *out = *prm;
+  out->dt = dt;
+  out->w_vel = prm->w_vel * r * r;
+  out->w_acc = prm->w_acc * pow(r, 4.0);
+  out->w_jerk = jerk ? prm->w_jerk * pow(r, 6.0) : 0.0;
+}
+
+/* the solve's best seed: lowest-cost collision-free, else lowest-cost */
+static int32_t solve_best(int32_t B, const double* cost, const uint8_t* cfree) {
+  int32_t bi = 0, bf = -1;
+  for (int32_t b = 0; b < B; ++b) {
+    if (cost[b] < cost[bi]) bi = b;
+    if (cfree[b] && (bf < 0 || cost[b] < cost[bf])) bf = b;
+  }
+  return bf >= 0 ? bf : bi;
+}
+
+int32_t cro_time_discretized_solve(const cro_robot* rb, const cro_world* w, const double* q_start,
+                                   const double* goal7, const double* goal_q, const cro_params* prm,
+                                   int32_t H, int32_t B, const double* seeds, int32_t iters1, int32_t iters2,
+                                   double dt_init, double dt_min, double w_pose, double w_jerk, double w_time,
+                                   double* first, double* stage, double* traj, double* cost, uint8_t* cfree,
+                                   double* dt, double* score) {
+  const size_t n = (size_t)H * rb->dof;
+  cro_params p1, p2;
+  /* 1. solve at the coarse step without the jerk term */
+  cro_time_scaled_params(prm, dt_init, 0, &p1);
+  double* x1 = (double*)malloc((size_t)B * n * sizeof(double));
+  double* c1 = (double*)malloc((size_t)B * sizeof(double));
+  uint8_t* f1 = (uint8_t*)malloc((size_t)B);
+  cro_solve(rb, w, q_start, goal7, goal_q, &p1, H, B, seeds, iters1, x1, c1, f1);
+  /* 2. retime the best seed; scale the weights to that step, jerk on */
+  int32_t b1 = solve_best(B, c1, f1);
+  double dt_opt = cro_retime(rb, H, q_start, x1 + (size_t)b1 * n);
+  if (dt_opt < dt_min) dt_opt = dt_min;
+  cro_time_scaled_params(prm, dt_opt, 1, &p2);
+  if (first) memcpy(first, x1 + (size_t)b1 * n, n * sizeof(double));
+  if (stage) {
+    stage[0] = p1.dt; stage[1] = p1.w_vel; stage[2] = p1.w_acc; stage[3] = p1.w_jerk;
+    stage[4] = p2.dt; stage[5] = p2.w_vel; stage[6] = p2.w_acc; stage[7] = p2.w_jerk;
+  }
+  /* 3. solve again from every seed of the first solve */
+  cro_solve(rb, w, q_start, goal7, goal_q, &p2, H, B, x1, iters2, traj, cost, cfree);
+  /* 4. retime every seed, score it at its own step, choose */
+  for (int32_t b = 0; b < B; ++b) dt[b] = cro_retime(rb, H, q_start, traj + (size_t)b * n);
+  int32_t chosen = cro_rank_seeds(rb, H, B, q_start, goal7, traj, cfree, dt, 0.0, 0, w_pose, w_jerk, w_time,
+                                  0.0, score);
+  if (chosen < 0) chosen = solve_best(B, cost, cfree);
+  free(x1); free(c1); free(f1);
+  return chosen;
+}

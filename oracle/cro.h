@@ -267,6 +267,37 @@ int32_t cro_rank_seeds(const cro_robot* rb, int32_t H, int32_t B, const double* 
                        const double* theta, const uint8_t* cfree, const double* dt, double dt_all,
                        int32_t ik, double w_pose, double w_jerk, double w_time, double w_dist, double* score);
 
+/* ------------------------------------------------------------------------ */
+/* Alg. "Time Discretization" (App. "Time-step Discretization")               */
+/* ------------------------------------------------------------------------ */
+
+/* The parameters for step dt: prm with dt replaced and the weight on the
+ * square of the k-th derivative (velocity k = 1, acceleration 2, jerk 3)
+ * multiplied by (dt / prm->dt)^(2k) (reading of "scale the weights by the
+ * new dt": the smoothness of the same waypoints keeps its value); jerk = 0
+ * sets the jerk weight to zero. */
+void cro_time_scaled_params(const cro_params* prm, double dt, int32_t jerk, cro_params* out);
+
+/* The whole algorithm for one problem, in its order:
+ *   1. cro_solve (iters1) with cro_time_scaled_params(prm, dt_init, no jerk);
+ *   2. the best seed of 1 (lowest-cost collision-free, else lowest-cost),
+ *      dt_opt = max(cro_retime(that seed), dt_min);
+ *   3. cro_solve (iters2) from every seed's best iterate of 1 with
+ *      cro_time_scaled_params(prm, dt_opt, jerk on);
+ *   4. dt[b] = cro_retime of every seed of 3; cro_rank_seeds with those steps
+ *      and the weights w_pose, w_jerk, w_time (App. "Solver details").
+ * Writes first [H][dof] (best of 1), stage [8] (dt and the velocity,
+ * acceleration and jerk weights of 1, then of 3), traj [B][H][dof], cost [B]
+ * and cfree [B] (the best iterates of 3), dt [B], score [B]; returns the
+ * chosen seed: the lowest score among the collision-free seeds, else the
+ * best seed of 3 by the rule of step 2. */
+int32_t cro_time_discretized_solve(const cro_robot* rb, const cro_world* w, const double* q_start,
+                                   const double* goal7, const double* goal_q, const cro_params* prm,
+                                   int32_t H, int32_t B, const double* seeds, int32_t iters1, int32_t iters2,
+                                   double dt_init, double dt_min, double w_pose, double w_jerk, double w_time,
+                                   double* first, double* stage, double* traj, double* cost, uint8_t* cfree,
+                                   double* dt, double* score);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1062,6 +1062,73 @@ def test_retime_scaling_and_limits(oracle_mod):
     assert oracle_mod.retime(rb, q0, np.tile(q0, (H, 1))) < 1e-6   # rounding residue only (cube root)
 
 
+def test_time_scaled_weights_keep_smoothness(oracle_mod):
+    """Reading of Alg. "Time Discretization"'s weight scaling: with the weight
+    on the square of the k-th derivative times (dt / dt0)^(2k), the Eq. 16
+    smoothness of the same waypoints is the same at every dt (the App. A.5
+    derivatives scale as 1/dt^k); without the jerk term only the
+    acceleration part is left."""
+    rb = _robot()
+    rng = np.random.default_rng(40)
+    qs = synth.uniform_config(rng, rb) * 0.3
+    th = synth.linear_seeds(rng, rb, qs, synth.uniform_config(rng, rb) * 0.3, 3, 12, noise=0.3)
+    w = synth.World(pose=np.zeros((0, 7)), half_ext=np.zeros((0, 3)))
+    goal = np.array([0, 0, 1.0, 1, 0, 0, 0])
+    base = dict(flags=oracle_mod.SPEED | oracle_mod.SWEPT, w_jerk=2.0)
+    ref = oracle_mod.evaluate(rb, w, qs, goal, th, base)["terms"][:, 3]
+    for dt in (0.01, 0.02, 0.25, 0.7):
+        p = oracle_mod.time_scaled_params(base, dt)
+        r = dt / 0.05
+        assert p["dt"] == dt and p["w_acc"] == pytest.approx(5000 * r ** 4, rel=1e-14)
+        assert p["w_jerk"] == pytest.approx(2.0 * r ** 6, rel=1e-14)
+        assert p["w_vel"] == pytest.approx(5000 * r ** 2, rel=1e-14)
+        got = oracle_mod.evaluate(rb, w, qs, goal, th, p)["terms"][:, 3]
+        np.testing.assert_allclose(got, ref, rtol=1e-9)
+        acc_only = oracle_mod.evaluate(rb, w, qs, goal, th, dict(base, w_jerk=0.0))["terms"][:, 3]
+        got = oracle_mod.evaluate(rb, w, qs, goal, th, oracle_mod.time_scaled_params(base, dt, jerk=False))
+        np.testing.assert_allclose(got["terms"][:, 3], acc_only, rtol=1e-9)
+
+
+def test_time_discretized_solve_stages(oracle_mod):
+    """Alg. "Time Discretization" as composed: the first solve is the plain
+    solve at the coarse step without jerk; dt_opt is the retimed step of its
+    best seed; the second solve starts from its seeds with the weights for
+    dt_opt; every seed is retimed, and the chosen one has the lowest score
+    among the collision-free seeds, which puts it exactly at a limit."""
+    rb = _robot()
+    rng = np.random.default_rng(41)
+    qs = synth.uniform_config(rng, rb) * 0.5
+    qg = synth.uniform_config(rng, rb) * 0.5
+    w = synth.make_world(3, 7, lambda p, h: oracle_mod.start_collides_with_box(rb, qs, p, h))
+    goal = oracle_mod.goal_pose_from_fk(rb, qg)
+    seeds = synth.linear_seeds(rng, rb, qs, qg, 4, 12, noise=0.2)
+    out = oracle_mod.time_discretized_solve(rb, w, qs, goal, seeds, 6, 6)
+    p1 = oracle_mod.time_scaled_params(None, 0.25, jerk=False)
+    s1 = oracle_mod.solve(rb, w, qs, goal, seeds, 6, p1)
+    c1, f1 = s1["cost"], s1["cfree"]
+    b1 = int(np.argmin(np.where(f1, c1, np.inf))) if f1.any() else int(np.argmin(c1))
+    np.testing.assert_array_equal(out["first"], s1["x"][b1])
+    dt_opt = max(oracle_mod.retime(rb, qs, s1["x"][b1]), 1e-3)
+    assert out["stage"][4] == dt_opt
+    p2 = oracle_mod.time_scaled_params(None, dt_opt, jerk=True)
+    np.testing.assert_array_equal(out["stage"], [p1["dt"], p1["w_vel"], p1["w_acc"], p1["w_jerk"],
+                                                 p2["dt"], p2["w_vel"], p2["w_acc"], p2["w_jerk"]])
+    assert p1["w_jerk"] == 0.0 and p2["w_jerk"] > 0.0
+    s2 = oracle_mod.solve(rb, w, qs, goal, s1["x"], 6, p2)
+    np.testing.assert_array_equal(out["traj"], s2["x"])
+    for b in range(4):
+        assert out["dt"][b] == oracle_mod.retime(rb, qs, out["traj"][b])
+    ok = np.where(out["cfree"], out["score"], np.inf)
+    if out["cfree"].any():
+        assert out["chosen"] == int(np.argmin(ok))
+        x = out["traj"][out["chosen"]]
+        v, a, j = oracle_mod.stencil(qs, x, out["dt"][out["chosen"]])
+        ratio = max(np.max(np.abs(v) / rb.v_max), np.max(np.abs(a) / rb.a_max), np.max(np.abs(j) / rb.j_max))
+        assert ratio == pytest.approx(1.0, rel=1e-9)
+    else:
+        assert out["chosen"] == int(np.argmin(out["cost"]))
+
+
 def _axis_angle(axis, phi):
     """Rotation matrix about a unit axis (Rodrigues), for the pose-error pins."""
     k = np.asarray(axis, dtype=np.float64)
