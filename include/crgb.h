@@ -315,6 +315,9 @@ typedef struct {
   float* cost;     /* [B] its cost */
   uint8_t* cfree;  /* [B] its collision-free flag */
   int32_t* best;   /* [1] index of the lowest-cost collision-free seed, else of the lowest-cost seed */
+  int32_t* status; /* [1] device status word, written on the stream with the results: CR_OK, or
+                      CR_ENAN when a seed's best cost is not finite (a seed with a NaN or infinite
+                      value, or an overflow); the other seeds' results stay valid */
 } cr_result;
 
 #define CR_SOLVE_GRAPH 1u       /* capture the whole solve as one CUDA graph, replayed on later calls */
@@ -334,6 +337,44 @@ typedef struct {
 cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
                    const cr_params* params, int32_t iters, uint32_t solve_flags,
                    const cr_result* results, void* stream);
+
+/* Alg. "Time Discretization" (App. "Time-step Discretization"): the
+ * trajectory is first optimised at a coarse step without the jerk term, then
+ * re-timed to the robot's limits and optimised again at that step.  Per
+ * problem, entirely on the device (no host round trip between the stages):
+ *   1. iters1 iterations (as cr_solve) at dt_init, the derivative weights
+ *      scaled to dt_init and the jerk weight 0;
+ *   2. the best seed of 1 (lowest-cost collision-free, else lowest-cost) is
+ *      retimed (cr_retime): dt_opt = max(its step, dt_min); the weight on the
+ *      square of the k-th derivative becomes w_k (dt_opt / dt)^(2k) with the
+ *      params' own dt and weights (the reading of "scale the weights by the
+ *      new dt": it keeps each term's value for the same waypoints), jerk on;
+ *   3. iters2 iterations at dt_opt from the best iterates of every seed of 1;
+ *   4. every seed of 3 is retimed and scored as cr_rank_seeds does with the
+ *      weights below; the chosen seed is the lowest score among the
+ *      collision-free seeds, else the solve's best.
+ * `results` receive the second solve's output as cr_solve writes it; tres
+ * (device buffers per problem, any may be NULL) the stages' outputs.
+ * Trajectory problems only (CR_IK_MODE is refused).  solve_flags as cr_solve
+ * (with CR_SOLVE_GRAPH the whole algorithm is one CUDA graph). */
+typedef struct {
+  float dt_init;     /* time step of the first solve [s] (the paper's coarse step: 0.25) */
+  float dt_min;      /* floor of the retimed step [s] */
+  int32_t iters1, iters2;
+  float w_pose, w_jerk, w_time;  /* seed-choice weights of cr_rank_seeds */
+} cr_timeopt_config;
+
+typedef struct {
+  float* first;    /* [H][dof] best trajectory of the first solve */
+  float* stage;    /* [8] dt, w_vel, w_acc, w_jerk used by the first solve, then by the second */
+  float* dt;       /* [B] each seed's retimed step after the second solve */
+  float* score;    /* [B] its seed-choice score */
+  int32_t* chosen; /* [1] the chosen seed */
+} cr_timeopt_result;
+
+cr_status cr_solve_timeopt(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
+                           const cr_params* params, const cr_timeopt_config* cfg, uint32_t solve_flags,
+                           const cr_result* results, const cr_timeopt_result* tres, void* stream);
 
 /* Autotuner: time cr_solve of this batch (`iters` iterations) for each tile
  * shape -- CTA size 256 or 512 threads; when a horizon is below 32, 8, 16,

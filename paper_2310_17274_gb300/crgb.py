@@ -61,7 +61,16 @@ class Problem(C.Structure):
 
 
 class Result(C.Structure):
-    _fields_ = [("traj", _vp), ("cost", _vp), ("cfree", _vp), ("best", _vp)]
+    _fields_ = [("traj", _vp), ("cost", _vp), ("cfree", _vp), ("best", _vp), ("status", _vp)]
+
+
+class TimeoptConfig(C.Structure):
+    _fields_ = [("dt_init", C.c_float), ("dt_min", C.c_float), ("iters1", C.c_int32),
+                ("iters2", C.c_int32), ("w_pose", C.c_float), ("w_jerk", C.c_float), ("w_time", C.c_float)]
+
+
+class TimeoptResult(C.Structure):
+    _fields_ = [("first", _vp), ("stage", _vp), ("dt", _vp), ("score", _vp), ("chosen", _vp)]
 
 
 SOLVE_GRAPH, SOLVE_PERSISTENT, SOLVE_DEVICE_SEEDS = 1, 2, 4
@@ -99,6 +108,9 @@ SIGNATURES = {
     "cr_retime": ([_vp, C.POINTER(Problem), C.c_int32, _vp, _vp, _vp], C.c_int32),
     "cr_rank_seeds": ([_vp, C.POINTER(Problem), C.POINTER(Params), C.c_int32, _vp, _vp, _vp, C.c_float,
                        C.c_float, C.c_float, C.c_float, _vp, _vp, _vp], C.c_int32),
+    "cr_solve_timeopt": ([_vp, _vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params),
+                          C.POINTER(TimeoptConfig), C.c_uint32, C.POINTER(Result), C.POINTER(TimeoptResult),
+                          _vp], C.c_int32),
     "cr_autotune": ([_vp, _vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), C.c_int32,
                      C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                      C.POINTER(C.c_float)], C.c_int32),
@@ -399,46 +411,45 @@ def rank_seeds(robot: Robot, problem: ProblemSpec, theta, cfree, params=None, dt
     return score, best
 
 
-def time_discretized_solve(ctx, robot: Robot, problem: ProblemSpec, params=None, iters=(100, 100),
-                           dt_init=0.25):
-    """Alg. "Time Discretization" (App. "Time-step Discretization") for one
-    problem: solve at dt_init without the jerk term; retime the best seed to
-    dt_opt (the step that puts it at the limits); scale the derivative weights
-    to dt_opt and enable jerk; solve again from the first solution at dt_opt;
-    retime every seed of the result; among the collision-free ones take the
-    lowest blend of pose error, largest jerk and motion time at its own time
-    step (App. "Solver details", rank_seeds).  Weights on the square of the
-    k-th derivative are multiplied by (dt / dt0)^(2k), dt0 the params' own dt,
-    so each term keeps the magnitude it has for the same trajectory at dt0 (the
-    paper says only that the weights are scaled by the new dt).
-    Returns (SolveOutput, dt_opt, dt_f, chosen): dt_f the chosen seed's time
-    step, chosen its index (the solve's own best when no seed is collision-free)."""
-    base = params_default()
-    if params:
-        base.update(params if isinstance(params, dict) else {})
-    dt0 = float(base["dt"])
+class TimeoptOutput:
+    """Device outputs of the stages of one problem's time-discretised solve."""
 
-    def scaled(dt, jerk):
-        p = dict(base)
-        r = dt / dt0
-        p["dt"] = dt
-        p["w_vel"] = base["w_vel"] * r ** 2
-        p["w_acc"] = base["w_acc"] * r ** 4
-        p["w_jerk"] = base["w_jerk"] * r ** 6 if jerk else 0.0
-        return make_params(p)
+    def __init__(self, n_seeds, horizon, dof, device="cuda"):
+        import torch
+        self.first = torch.empty((horizon, dof), device=device)
+        self.stage = torch.empty(8, device=device)
+        self.dt = torch.empty(n_seeds, device=device)
+        self.score = torch.empty(n_seeds, device=device)
+        self.chosen = torch.empty(1, device=device, dtype=torch.int32)
+        self._struct = TimeoptResult(_dptr(self.first), _dptr(self.stage), _dptr(self.dt), _dptr(self.score),
+                                     _dptr(self.chosen))
 
-    o1 = solve(ctx, robot, [problem], scaled(dt_init, False), iters=iters[0])[0]
-    b1 = int(o1.best)
-    dt_opt = float(retime(robot, problem, o1.traj[b1:b1 + 1])[0])
-    dt_opt = max(dt_opt, 1e-3)
-    o2 = solve(ctx, robot, [problem], scaled(dt_opt, True), iters=iters[1],
-               device_seeds=[o1.traj.contiguous()])[0]
-    dts = retime(robot, problem, o2.traj)
-    _, chosen = rank_seeds(robot, problem, o2.traj, o2.cfree, scaled(dt_opt, True), dt=dts)
-    b2 = int(chosen)
-    if b2 < 0:
-        b2 = max(int(o2.best), 0)
-    return o2, dt_opt, float(dts[b2]), b2
+    def struct(self) -> TimeoptResult:
+        return self._struct
+
+
+def time_discretized_solve(ctx, robot: Robot, problems, params=None, iters=(100, 100), dt_init=0.25,
+                           dt_min=1e-3, w_pose=1.0, w_jerk=1e-3, w_time=1.0, graph=True, persistent=True,
+                           stream=None):
+    """Alg. "Time Discretization" through cr_solve_timeopt (every stage on the
+    device, include/crgb.h).  problems: one ProblemSpec (host seeds) or a list.
+    Returns, per problem, (SolveOutput of the second solve, TimeoptOutput)."""
+    single = isinstance(problems, ProblemSpec)
+    probs = [problems] if single else list(problems)
+    n = len(probs)
+    arr = (Problem * n)(*[p.struct() for p in probs])
+    outs = [SolveOutput(p.struct().n_seeds, p.horizon, robot.dof) for p in probs]
+    touts = [TimeoptOutput(p.struct().n_seeds, p.horizon, robot.dof) for p in probs]
+    res = (Result * n)(*[o.struct() for o in outs])
+    tres = (TimeoptResult * n)(*[o.struct() for o in touts])
+    cfg = TimeoptConfig(float(dt_init), float(dt_min), int(iters[0]), int(iters[1]), float(w_pose),
+                        float(w_jerk), float(w_time))
+    P = params if isinstance(params, Params) else make_params(params)
+    flags = (SOLVE_GRAPH if graph else 0) | (SOLVE_PERSISTENT if persistent else 0)
+    check(lib().cr_solve_timeopt(ctx.handle, robot.handle, n, arr, C.byref(P), C.byref(cfg), flags, res, tres,
+                                 _stream(stream)), "cr_solve_timeopt")
+    pairs = list(zip(outs, touts))
+    return pairs[0] if single else pairs
 
 
 class OptBuffers:
@@ -512,7 +523,9 @@ class SolveOutput:
         self.cost = torch.empty(n_seeds, device=device)
         self.cfree = torch.empty(n_seeds, device=device, dtype=torch.uint8)
         self.best = torch.empty(1, device=device, dtype=torch.int32)
-        self._struct = Result(_dptr(self.traj), _dptr(self.cost), _dptr(self.cfree), _dptr(self.best))
+        self.status = torch.empty(1, device=device, dtype=torch.int32)
+        self._struct = Result(_dptr(self.traj), _dptr(self.cost), _dptr(self.cfree), _dptr(self.best),
+                              _dptr(self.status))
 
     def struct(self) -> Result:
         return self._struct

@@ -338,7 +338,7 @@ cr_status check_params(const cr_params* p) {
   return CR_OK;
 }
 
-cr_status fill_problem(const cr_robot* rb, const cr_problem* pr, ProblemView* pv) {
+cr_status fill_problem(const cr_robot* rb, const cr_problem* pr, ProblemView* pv, const cr_params* prm) {
   if (!pr || !pr->world || !pr->q_start || !pr->goal) return fail(CR_EINVAL, "problem: null field");
   if (pr->horizon < 1 || pr->horizon > kMaxHorizon)
     return fail(CR_EINVAL, "horizon %d outside 1..%d", pr->horizon, kMaxHorizon);
@@ -354,6 +354,12 @@ cr_status fill_problem(const cr_robot* rb, const cr_problem* pr, ProblemView* pv
   if (pr->goal_q) {
     pv->has_goal_q = 1;
     for (int j = 0; j < rb->dof; ++j) pv->goal_q[j] = pr->goal_q[j];
+  }
+  if (prm) {
+    pv->dt = prm->dt;
+    pv->w_vel = prm->w_vel;
+    pv->w_acc = prm->w_acc;
+    pv->w_jerk = prm->w_jerk;
   }
   return CR_OK;
 }
@@ -381,7 +387,7 @@ cr_status cr_eval(const cr_robot* robot, const cr_problem* problem, const cr_par
   if (B > 0 && (!theta || !cost)) return fail(CR_EINVAL, "cr_eval: null theta or cost");
   EvalArgs a{};
   std::memset(&a, 0, sizeof(a));
-  s = fill_problem(robot, problem, &a.prob0);
+  s = fill_problem(robot, problem, &a.prob0, params);
   if (s != CR_OK) return s;
   if (B == 0) return CR_OK;
   const int H = problem->horizon;

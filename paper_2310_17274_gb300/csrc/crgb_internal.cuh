@@ -87,6 +87,10 @@ struct ProblemView {
   float goal_R[9];     // row-major
   float goal_q[kMaxDof];  // Eq. 15 goal configuration when has_goal_q
   int has_goal_q;
+  // time step and the weights of the derivative terms of Eq. 16 for this
+  // problem (the parameters' values, or those a time-discretised solve sets
+  // on the device between its two solves)
+  float dt, w_vel, w_acc, w_jerk;
 };
 
 // Arguments of the fused evaluation kernel.
@@ -197,14 +201,34 @@ struct ResultView {
   float* cost;
   uint8_t* cfree;
   int* best;
+  int* status;  // CR_OK, or CR_ENAN when a seed's best cost is not finite
   int n_seeds, n, seed_base, var_base;
+};
+
+// Per-problem outputs of the time-discretised solve (runtime.cu, k_time.cu);
+// any may be nullptr.
+struct TimeoptView {
+  float* first;   // [H][dof] best trajectory of the first solve
+  float* stage;   // [8] dt, w_vel, w_acc, w_jerk of the first, then of the second solve
+  float* dt;      // [B] each seed's retimed step after the second solve
+  float* score;   // [B] seed-choice score
+  int* chosen;    // [1] chosen seed
+};
+
+// Reading of "scale the weights by the new dt" (Alg. "Time Discretization"):
+// the weight on the square of the k-th derivative times (dt / dt0)^(2k).
+struct TimeScale {
+  float dt0, w_vel0, w_acc0, w_jerk0;  // the parameters' own step and weights
+  float dt_min;                        // floor of the retimed step
+  float rank_pose, rank_jerk, rank_time;  // seed-choice weights (App. "Solver details")
 };
 
 // launch helpers (k_eval.cu / k_opt.cu / runtime.cu)
 cudaError_t launch_finish(const ResultView* res, int n_problems, const float* best_x,
                           const float* best_c, const uint8_t* best_cfree, cudaStream_t s);
 cr_status check_params(const cr_params* p);
-cr_status fill_problem(const cr_robot* rb, const cr_problem* pr, ProblemView* pv);
+cr_status fill_problem(const cr_robot* rb, const cr_problem* pr, ProblemView* pv,
+                       const cr_params* prm);
 cudaError_t launch_fk(const RobotView& rb, const float* theta, int n, float* spheres, float* ee,
                       float* link_tf, cudaStream_t stream);
 cudaError_t launch_eval(const EvalArgs& a, int grid, int block, cudaStream_t stream);
@@ -217,6 +241,25 @@ cudaError_t launch_eval_ik(const EvalArgs& a, cudaStream_t stream);
 int eval_ik_smem_bytes(int dof);
 int eval_ik_blocks_per_sm(int dof);
 cudaError_t launch_opt(const OptArgs& a, int n_max, cudaStream_t stream);
+// time-discretised solve, between the two solves and after the second:
+// k_time.cu (one CTA per problem)
+cudaError_t launch_timeopt_mid(ProblemView* px, ProblemView* pc, int n_problems, const TimeoptView* tv,
+                               const RobotView& rb, const float* best_x, const float* best_c,
+                               const uint8_t* best_cfree, float* x, const TimeScale& sc, cudaStream_t s);
+cudaError_t launch_timeopt_final(const ProblemView* px, int n_problems, const TimeoptView* tv,
+                                 const RobotView& rb, const float* best_x, const float* best_c,
+                                 const uint8_t* best_cfree, float* ws_dt, float* ws_score,
+                                 const TimeScale& sc, cudaStream_t s);
+// the time step and weights the scale gives for dt (jerk on or off); the same
+// arithmetic on the host (first solve) and the device (second solve)
+__host__ __device__ inline void time_scaled(const TimeScale& sc, float dt, bool jerk, float* out4) {
+  const float r = dt / sc.dt0;
+  const float r2 = r * r;
+  out4[0] = dt;
+  out4[1] = sc.w_vel0 * r2;
+  out4[2] = sc.w_acc0 * (r2 * r2);
+  out4[3] = jerk ? sc.w_jerk0 * (r2 * r2 * r2) : 0.f;
+}
 int opt_smem_bytes(int history, int n_max);
 
 cr_status set_error(cr_status code, const char* msg);

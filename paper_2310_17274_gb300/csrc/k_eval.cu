@@ -74,7 +74,6 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   const bool store_x = a.store_x != 0;
   const float eta = prm.eta, inv_eta = 1.f / prm.eta;
   const float e2 = prm.eta_bound, inv_e2 = 1.f / prm.eta_bound;
-  const float dt = prm.dt, inv2dt = 0.5f / dt;
 
   EvalSmem L;
   L.build(D, M, P, G, a.max_traj, a.max_states, nw, store_x);
@@ -178,6 +177,9 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     __syncthreads();
     const int H = s_prob.horizon;
     const int K = s_prob.n_boxes;
+    // time step and derivative weights of this problem
+    const float dt = s_prob.dt, inv2dt = 0.5f / dt;
+    const float w_vel = s_prob.w_vel, w_acc = s_prob.w_acc, w_jerk = s_prob.w_jerk;
     const int S = nt * H;
     const long long vbase = s_prob.var_base + (long long)r0 * H * D;
 
@@ -726,11 +728,11 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
         const float vel = (qm2 - 8.f * qm1 + 8.f * qp1 - qp2) * inv12dt;
         const float accl = (-qm2 + 16.f * qm1 - 30.f * q0 + 16.f * qp1 - qp2) * inv12dt2;
         const float jrk = (-qm2 + 2.f * qm1 - 2.f * qp1 + qp2) * inv2dt3;
-        float sm = prm.w_acc * accl * accl + prm.w_jerk * jrk * jrk;
-        float dv = 0.f, da = 2.f * prm.w_acc * accl, dj = 2.f * prm.w_jerk * jrk;
+        float sm = w_acc * accl * accl + w_jerk * jrk * jrk;
+        float dv = 0.f, da = 2.f * w_acc * accl, dj = 2.f * w_jerk * jrk;
         if (flags & CR_VEL_COST) {
-          sm += prm.w_vel * logcoshf(prm.k_vel * vel);
-          dv += prm.w_vel * prm.k_vel * tanhf(prm.k_vel * vel);
+          sm += w_vel * logcoshf(prm.k_vel * vel);
+          dv += w_vel * prm.k_vel * tanhf(prm.k_vel * vel);
         }
         float s1, s2, s3;
         const float vm = s_lim[2 * D + j], am = s_lim[3 * D + j], jm = s_lim[4 * D + j];

@@ -9,14 +9,11 @@
 
 #include "crgb_internal.cuh"
 #include "k_device.cuh"
+#include "k_time.cuh"
 
 namespace crgb {
 
 namespace {
-
-struct RankWeights {
-  float pose, jerk, time, dist;
-};
 
 __global__ void k_rank_score(RobotView rb, ProblemView pv, const float* __restrict__ theta, int B,
                              const float* __restrict__ dt, float dt_all, int ik, RankWeights w,
@@ -29,59 +26,7 @@ __global__ void k_rank_score(RobotView rb, ProblemView pv, const float* __restri
   __syncthreads();
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
-  const float* th = theta + (long long)b * H * D;
-  const float* last = th + (H - 1) * D;
-  // end effector of the last state: T_{dof-1} F_ee
-  float T[12] = {1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f};
-  for (int l = 0; l < D; ++l) {
-    float sn, cs;
-    sincosf(last[l], &sn, &cs);
-    float N[12];
-    fk_joint(s_fix + 12 * l, s_axis[l], sn, cs, T, N);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) T[k] = N[k];
-  }
-  const float* Fe = s_fix + D * 12;
-  float E[12];
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const float v = fmaf(T[4 * r], Fe[c], fmaf(T[4 * r + 1], Fe[4 + c], T[4 * r + 2] * Fe[8 + c]));
-      E[4 * r + c] = c == 3 ? v + T[4 * r + 3] : v;
-    }
-  const V3 e = v3(E[3] - pv.goal_p[0], E[7] - pv.goal_p[1], E[11] - pv.goal_p[2]);
-  float tr = 0.f;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) tr = fmaf(pv.goal_R[a * 3 + c], E[a * 4 + c], tr);
-  float s = w.pose * (norm(e) + (3.f - tr) * 0.25f);
-  if (ik) {
-    float d2 = 0.f;
-    for (int j = 0; j < D; ++j) {
-      const float d = last[j] - pv.q_start[j];
-      d2 = fmaf(d, d, d2);
-    }
-    s += w.dist * sqrtf(d2);
-  } else {
-    // largest |jerk| of App. A.5's five-point stencil over the padded sequence
-    // (three copies of q_start, theta_1..theta_H, two copies of theta_H)
-    const float dtb = dt ? dt[b] : dt_all;
-    auto ext = [&](int n, int j) -> float {
-      if (n <= 2) return pv.q_start[j];
-      if (n >= H + 2) return th[(H - 1) * D + j];
-      return th[(n - 3) * D + j];
-    };
-    float jm = 0.f;
-    for (int e2 = 2; e2 <= H + 2; ++e2)
-      for (int j = 0; j < D; ++j) {
-        const float jr = (-ext(e2 - 2, j) + 2.f * ext(e2 - 1, j) - 2.f * ext(e2 + 1, j) + ext(e2 + 2, j)) * 0.5f;
-        jm = fmaxf(jm, fabsf(jr));
-      }
-    s += w.jerk * (jm / (dtb * dtb * dtb)) + w.time * (float)H * dtb;
-  }
-  score[b] = s;
+  score[b] = seed_score(s_fix, s_axis, D, pv, theta + (long long)b * H * D, dt ? dt[b] : dt_all, ik, w);
 }
 
 // The lowest score among collision-free seeds, the lowest index on ties; -1
@@ -92,10 +37,10 @@ __global__ void k_rank_best(const float* __restrict__ score, const uint8_t* __re
   __shared__ int s_i[32];
   float bs = INFINITY;
   int bi = -1;
-  auto better = [](float s, int i, float bs, int bi) { return bi < 0 || s < bs || (s == bs && i < bi); };
+  auto better = [](float s, int i, float bs, int bi) { return score_better(s, i, bs, bi); };
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
     const float s = score[b];
-    if (cfree[b] && !isnan(s) && better(s, b, bs, bi)) {
+    if (cfree[b] && better(s, b, bs, bi)) {
       bs = s;
       bi = b;
     }
@@ -142,7 +87,7 @@ extern "C" cr_status cr_rank_seeds(const cr_robot* robot, const cr_problem* prob
   const int ik = (params->flags & CR_IK_MODE) != 0;
   if (!ik && !dt && !(params->dt > 0.f)) return set_error(CR_EINVAL, "cr_rank_seeds: dt must be > 0");
   ProblemView pv;
-  cr_status st = fill_problem(robot, problem, &pv);
+  cr_status st = fill_problem(robot, problem, &pv, params);
   if (st != CR_OK) return st;
   const cudaStream_t s = (cudaStream_t)stream;
   if (B > 0) {

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "crgb_internal.cuh"
+#include "k_time.cuh"
 
 namespace crgb {
 
@@ -18,27 +19,8 @@ __global__ void k_retime(RobotView rb, ProblemView pv, const float* __restrict__
   const int lane = threadIdx.x & 31;
   const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (b >= B) return;
-  const int D = rb.dof, H = pv.horizon, NS = H + 1;
-  const float* th = theta + (long long)b * H * D;
-  // padded sequence of App. A.5: three copies of q_start, theta_1..theta_H, two copies of theta_H
-  auto ext = [&](int n, int j) -> float {
-    if (n <= 2) return pv.q_start[j];
-    if (n >= H + 2) return th[(H - 1) * D + j];
-    return th[(n - 3) * D + j];
-  };
-  float dt = 0.f;
-  for (int k = lane; k < NS * D; k += 32) {
-    const int e = k / D + 2, j = k % D;
-    const float qm2 = ext(e - 2, j), qm1 = ext(e - 1, j), q0 = ext(e, j), qp1 = ext(e + 1, j),
-                qp2 = ext(e + 2, j);
-    const float v = (qm2 - 8.f * qm1 + 8.f * qp1 - qp2) * (1.f / 12.f);
-    const float a = (-qm2 + 16.f * qm1 - 30.f * q0 + 16.f * qp1 - qp2) * (1.f / 12.f);
-    const float jr = (-qm2 + 2.f * qm1 - 2.f * qp1 + qp2) * 0.5f;
-    const float vm = rb.lim[2 * D + j], am = rb.lim[3 * D + j], jm = rb.lim[4 * D + j];
-    dt = fmaxf(dt, fabsf(v) / vm);
-    dt = fmaxf(dt, sqrtf(fabsf(a) / am));
-    dt = fmaxf(dt, cbrtf(fabsf(jr) / jm));
-  }
+  const int D = rb.dof, H = pv.horizon;
+  float dt = retime_part(theta + (long long)b * H * D, pv.q_start, rb.lim, H, D, lane, 32);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dt = fmaxf(dt, __shfl_xor_sync(0xffffffffu, dt, o));
   if (lane == 0) dt_out[b] = dt;
@@ -57,7 +39,7 @@ extern "C" cr_status cr_retime(const cr_robot* robot, const cr_problem* problem,
   if (B == 0) return CR_OK;
   if (!theta || !dt) return set_error(CR_EINVAL, "cr_retime: null buffer");
   ProblemView pv;
-  cr_status st = fill_problem(robot, problem, &pv);
+  cr_status st = fill_problem(robot, problem, &pv, nullptr);
   if (st != CR_OK) return st;
   const int warps = 8;
   k_retime<<<(B + warps - 1) / warps, 32 * warps, 0, (cudaStream_t)stream>>>(robot->view, pv, theta, B, dt);

@@ -24,7 +24,6 @@ using namespace crgb;
 
 namespace crgb {
 cr_status check_params(const cr_params* p);
-cr_status fill_problem(const cr_robot* rb, const cr_problem* pr, ProblemView* pv);
 }  // namespace crgb
 
 namespace {
@@ -92,7 +91,7 @@ extern "C" cr_status cr_eval_batch_noalloc(const cr_robot* robot, int32_t n_prob
   long long vo = 0;
   int tb = 0, max_traj = 0, max_states = 0, max_h = 0;
   for (int p = 0; p < n_problems; ++p) {
-    s = fill_problem(robot, &problems[p], &pv[p]);
+    s = fill_problem(robot, &problems[p], &pv[p], params);
     if (s != CR_OK) return s;
     if (n_traj[p] < 0) return fail(CR_EINVAL, "cr_eval_batch_noalloc: n_traj < 0");
     const int H = problems[p].horizon;

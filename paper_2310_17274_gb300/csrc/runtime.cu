@@ -27,7 +27,6 @@ using namespace crgb;
 
 namespace crgb {
 cr_status check_params(const cr_params* p);
-cr_status fill_problem(const cr_robot* rb, const cr_problem* pr, ProblemView* pv);
 }  // namespace crgb
 
 namespace {
@@ -59,8 +58,10 @@ __global__ void k_finish(const ResultView* res, int n_problems, const float* bes
   if (threadIdx.x == 0) {
     int bi = 0, bf = -1;
     float bc = INFINITY, fc = INFINITY;
+    bool finite = true;
     for (int b = 0; b < r.n_seeds; ++b) {
       const float c = best_c[r.seed_base + b];
+      finite = finite && isfinite(c);
       if (c < bc) {
         bc = c;
         bi = b;
@@ -72,6 +73,8 @@ __global__ void k_finish(const ResultView* res, int n_problems, const float* bes
     }
     s_best = bf >= 0 ? bf : bi;
     if (r.best) *r.best = s_best;
+    // a seed whose best cost is not finite (a non-finite seed, or an overflow)
+    if (r.status) *r.status = finite ? CR_OK : CR_ENAN;
   }
   __syncthreads();
   const long long total = (long long)r.n_seeds * r.n;
@@ -126,8 +129,16 @@ struct Plan {
   int no_store_x = 0;
   // workspace offsets (bytes)
   size_t o_x, o_g, o_xp, o_gp, o_dir, o_bx, o_c, o_bc, o_rho, o_it, o_s, o_y, o_cand, o_cgrad,
-      o_ccost, o_cfree, o_bfree, o_ls, o_queue, ws_bytes;
-  size_t o_tx, o_tc, o_px, o_pc, o_seed, o_res, tab_bytes;
+      o_ccost, o_cfree, o_bfree, o_ls, o_queue, o_tdt, o_tsc, ws_bytes;
+  size_t o_tx, o_tc, o_px, o_pc, o_seed, o_res, o_tv, tab_bytes;
+};
+
+// A time-discretised solve (Alg. "Time Discretization"): two solves with the
+// device steps of k_time.cu between and after them.
+struct TimeoptPlan {
+  TimeScale sc;
+  int iters1 = 0, iters2 = 0;
+  std::vector<TimeoptView> views;
 };
 
 struct cr_ctx {
@@ -177,7 +188,7 @@ int4 tuned(const cr_ctx* ctx, int M, int K, int H) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* pr,
-                     const cr_params* prm, const cr_result* res, Plan& pl) {
+                     const cr_params* prm, const cr_result* res, const TimeoptPlan* to, Plan& pl) {
   pl.P = P;
   pl.dof = rb->dof;
   pl.m = prm->history;
@@ -190,7 +201,7 @@ cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* p
   for (int p = 0; p < P; ++p) {
     if (pr[p].n_seeds < 1) return failf(CR_EINVAL, "problem %d: n_seeds < 1", p);
     ProblemView pv;
-    cr_status s = fill_problem(rb, &pr[p], &pv);
+    cr_status s = fill_problem(rb, &pr[p], &pv, prm);
     if (s != CR_OK) return s;
     const int H = pr[p].horizon, B = pr[p].n_seeds, n = H * rb->dof;
     if (n > 2048) return failf(CR_EINVAL, "problem %d: horizon * dof = %d > 2048", p, n);
@@ -211,6 +222,7 @@ cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* p
     rv.cost = res ? res[p].cost : nullptr;
     rv.cfree = res ? res[p].cfree : nullptr;
     rv.best = res ? res[p].best : nullptr;
+    rv.status = res ? res[p].status : nullptr;
     rv.n_seeds = B;
     rv.n = n;
     rv.seed_base = sb;
@@ -259,6 +271,7 @@ cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* p
   pl.o_y = take(V * m * 4); pl.o_cand = take(V * na * 4); pl.o_cgrad = take(V * na * 4);
   pl.o_ccost = take(S * na * 4); pl.o_cfree = take(S * na); pl.o_bfree = take(S);
   pl.o_ls = take(S * 4); pl.o_queue = take(256);
+  pl.o_tdt = take(to ? S * 4 : 0); pl.o_tsc = take(to ? S * 4 : 0);
   pl.ws_bytes = o;
   o = 0;
   pl.o_tx = take(pl.tiles_x.size() * sizeof(int4));
@@ -267,6 +280,7 @@ cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* p
   pl.o_pc = take(P * sizeof(ProblemView));
   pl.o_seed = take(pl.seedtab.size() * sizeof(int4));
   pl.o_res = take(P * sizeof(ResultView));
+  pl.o_tv = take(to ? P * sizeof(TimeoptView) : 0);
   pl.tab_bytes = o;
   if (ctx->mem_budget && pl.ws_bytes + pl.tab_bytes > ctx->mem_budget)
     return failf(CR_ENOMEM, "batch needs %zu bytes > context budget %zu", pl.ws_bytes + pl.tab_bytes,
@@ -300,10 +314,11 @@ cr_opt_state state_of(const Plan& pl, unsigned char* ws) {
   return st;
 }
 
-// Enqueue the iterations on `s` (eagerly or under capture).
+// Enqueue the iterations on `s` (eagerly or under capture); with `finish`
+// the per-problem results are written at the end.
 cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* prm, const Plan& pl,
                              unsigned char* ws, unsigned char* tab, int iters, bool persistent,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool finish = true) {
   const cr_opt_state st = state_of(pl, ws);
   int* queue = (int*)(ws + pl.o_queue);
   auto eval_args = [&](bool cand) {
@@ -378,15 +393,43 @@ cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* p
     o.early_loads = 1;  // follows the candidate evaluation directly
     RT_CUDA(launch_opt(o, pl.n_max, s));
   }
-  RT_CUDA(launch_finish((const ResultView*)(tab + pl.o_res), pl.P, st.best_x, st.best_c,
-                        st.best_cfree, s));
+  if (finish)
+    RT_CUDA(launch_finish((const ResultView*)(tab + pl.o_res), pl.P, st.best_x, st.best_c,
+                          st.best_cfree, s));
+  return CR_OK;
+}
+
+// Alg. "Time Discretization" on `s`: the first solve (the tables hold the
+// first step and weights), the device step that retimes each problem's best
+// seed and rewrites the tables for the second solve, the second solve from
+// every seed's best iterate, then every seed retimed, scored and chosen.
+cr_status enqueue_timeopt(cr_ctx* ctx, const cr_robot* rb, const cr_params* prm, const Plan& pl,
+                          const TimeoptPlan& to, unsigned char* ws, unsigned char* tab, bool persistent,
+                          cudaStream_t s) {
+  const cr_opt_state st = state_of(pl, ws);
+  const TimeoptView* tv = (const TimeoptView*)(tab + pl.o_tv);
+  cr_status rs = enqueue_iterations(ctx, rb, prm, pl, ws, tab, to.iters1, persistent, s, false);
+  if (rs != CR_OK) return rs;
+  RT_CUDA(launch_timeopt_mid((ProblemView*)(tab + pl.o_px), (ProblemView*)(tab + pl.o_pc), pl.P, tv, rb->view,
+                             st.best_x, st.best_c, st.best_cfree, st.x, to.sc, s));
+  rs = enqueue_iterations(ctx, rb, prm, pl, ws, tab, to.iters2, persistent, s, true);
+  if (rs != CR_OK) return rs;
+  RT_CUDA(launch_timeopt_final((const ProblemView*)(tab + pl.o_px), pl.P, tv, rb->view, st.best_x, st.best_c,
+                               st.best_cfree, (float*)(ws + pl.o_tdt), (float*)(ws + pl.o_tsc), to.sc, s));
   return CR_OK;
 }
 
 std::string graph_key(const cr_robot* rb, const cr_params* prm, const Plan& pl, int iters,
-                      bool persistent, const void* ws, const void* tab, int block) {
+                      bool persistent, const void* ws, const void* tab, int block, const TimeoptPlan* to) {
   std::string k;
   auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
+  const int kind = to ? 1 : 0;
+  put(&kind, sizeof(kind));
+  if (to) {
+    put(&to->sc, sizeof(to->sc));
+    put(&to->iters1, sizeof(int));
+    put(&to->iters2, sizeof(int));
+  }
   put(&rb, sizeof(rb));
   put(prm, sizeof(*prm));
   put(&iters, sizeof(iters));
@@ -430,9 +473,14 @@ cr_status cr_context_create(int device, size_t mem_budget, cr_ctx** out) {
 
 void cr_context_destroy(cr_ctx* c) { delete c; }
 
-cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
-                   const cr_params* params, int32_t iters, uint32_t solve_flags,
-                   const cr_result* results, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// The body of cr_solve and cr_solve_timeopt (to != nullptr).
+cr_status solve_impl(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
+                     const cr_params* params, int32_t iters, uint32_t solve_flags, const cr_result* results,
+                     void* stream, const TimeoptPlan* to) {
   if (!ctx || !robot || !problems || n_problems < 1) return failf(CR_EINVAL, "cr_solve: bad argument");
   if (iters < 0) return failf(CR_EINVAL, "cr_solve: iters < 0");
   cr_status s = check_params(params);
@@ -440,7 +488,7 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
   for (int p = 0; p < n_problems; ++p)
     if (!problems[p].seeds) return failf(CR_EINVAL, "problem %d: null seeds", p);
   Plan pl;
-  s = build_plan(ctx, robot, n_problems, problems, params, results, pl);
+  s = build_plan(ctx, robot, n_problems, problems, params, results, to, pl);
   if (s != CR_OK) return s;
   if (opt_smem_bytes(params->history, pl.n_max) > 200 * 1024)
     return failf(CR_EINVAL, "history * horizon * dof too large for shared memory");
@@ -481,6 +529,7 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
   std::memcpy(h + pl.o_pc, pl.probs_c.data(), pl.P * sizeof(ProblemView));
   std::memcpy(h + pl.o_seed, pl.seedtab.data(), pl.seedtab.size() * sizeof(int4));
   std::memcpy(h + pl.o_res, pl.results.data(), pl.P * sizeof(ResultView));
+  if (to) std::memcpy(h + pl.o_tv, to->views.data(), pl.P * sizeof(TimeoptView));
   RT_CUDA(cudaMemcpyAsync(tab, h, pl.tab_bytes, cudaMemcpyHostToDevice, st));
   // seeds -> x (host memory, or device memory with CR_SOLVE_DEVICE_SEEDS)
   if (host_seeds) {
@@ -498,10 +547,12 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
   }
   RT_CUDA(cudaEventRecord(ctx->staged, st));
   const bool persistent = (solve_flags & CR_SOLVE_PERSISTENT) != 0;
-  if (!(solve_flags & CR_SOLVE_GRAPH)) {
-    return enqueue_iterations(ctx, robot, params, pl, ws, tab, iters, persistent, st);
-  }
-  const std::string key = graph_key(robot, params, pl, iters, persistent, ws, tab, pl.block);
+  auto enqueue = [&](cudaStream_t q) {
+    return to ? enqueue_timeopt(ctx, robot, params, pl, *to, ws, tab, persistent, q)
+              : enqueue_iterations(ctx, robot, params, pl, ws, tab, iters, persistent, q);
+  };
+  if (!(solve_flags & CR_SOLVE_GRAPH)) return enqueue(st);
+  const std::string key = graph_key(robot, params, pl, iters, persistent, ws, tab, pl.block, to);
   cudaGraphExec_t exec = nullptr;
   for (auto& g : ctx->graphs)
     if (g.first == key) exec = g.second;
@@ -513,7 +564,7 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
     RT_CUDA(cudaStreamWaitEvent(ctx->cap, ev, 0));
     cudaEventDestroy(ev);
     RT_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
-    cr_status cs = enqueue_iterations(ctx, robot, params, pl, ws, tab, iters, persistent, ctx->cap);
+    cr_status cs = enqueue(ctx->cap);
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(ctx->cap, &graph);
     if (cs != CR_OK) {
@@ -532,6 +583,61 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
   }
   RT_CUDA(cudaGraphLaunch(exec, st));
   return CR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
+                   const cr_params* params, int32_t iters, uint32_t solve_flags,
+                   const cr_result* results, void* stream) {
+  return solve_impl(ctx, robot, n_problems, problems, params, iters, solve_flags, results, stream, nullptr);
+}
+
+cr_status cr_solve_timeopt(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
+                           const cr_params* params, const cr_timeopt_config* cfg, uint32_t solve_flags,
+                           const cr_result* results, const cr_timeopt_result* tres, void* stream) {
+  if (!cfg) return failf(CR_EINVAL, "cr_solve_timeopt: null config");
+  cr_status s = check_params(params);
+  if (s != CR_OK) return s;
+  if (params->flags & CR_IK_MODE) return failf(CR_EINVAL, "cr_solve_timeopt: not for IK-mode problems");
+  if (!(cfg->dt_init > 0.f) || !(cfg->dt_min > 0.f))
+    return failf(CR_EINVAL, "cr_solve_timeopt: dt_init and dt_min must be > 0");
+  if (cfg->iters1 < 0 || cfg->iters2 < 0) return failf(CR_EINVAL, "cr_solve_timeopt: iterations < 0");
+  TimeoptPlan to;
+  to.sc.dt0 = params->dt;
+  to.sc.w_vel0 = params->w_vel;
+  to.sc.w_acc0 = params->w_acc;
+  to.sc.w_jerk0 = params->w_jerk;
+  to.sc.dt_min = cfg->dt_min;
+  to.sc.rank_pose = cfg->w_pose;
+  to.sc.rank_jerk = cfg->w_jerk;
+  to.sc.rank_time = cfg->w_time;
+  to.iters1 = cfg->iters1;
+  to.iters2 = cfg->iters2;
+  to.views.resize(n_problems > 0 ? n_problems : 0);
+  for (int p = 0; p < n_problems; ++p) {
+    TimeoptView v{};
+    if (tres) {
+      v.first = tres[p].first;
+      v.stage = tres[p].stage;
+      v.dt = tres[p].dt;
+      v.score = tres[p].score;
+      v.chosen = tres[p].chosen;
+    }
+    to.views[p] = v;
+  }
+  // the first solve's step and weights (no jerk term) go into the tables
+  cr_params p1 = *params;
+  float w1[4];
+  time_scaled(to.sc, cfg->dt_init, false, w1);
+  p1.dt = w1[0];
+  p1.w_vel = w1[1];
+  p1.w_acc = w1[2];
+  p1.w_jerk = w1[3];
+  return solve_impl(ctx, robot, n_problems, problems, &p1, cfg->iters1 + cfg->iters2, solve_flags, results,
+                    stream, &to);
 }
 
 }  // extern "C"

@@ -225,7 +225,7 @@ cr_status slot_view(cr_server* sv, Pool& pl, int s, const Request& r, ProblemVie
   pr.goal = r.goal.data();
   pr.n_seeds = pl.B;
   pr.horizon = pl.H;
-  cr_status st = fill_problem(sv->robot, &pr, v);
+  cr_status st = fill_problem(sv->robot, &pr, v, &pl.prm);
   if (st != CR_OK) return st;
   v->n_traj = pl.B;
   v->traj_base = s * pl.B;
@@ -410,6 +410,7 @@ cr_status step_kind(cr_server* sv, Pool& pl) {
     rv.cost = (float*)(r0 + rl.cost);
     rv.cfree = (uint8_t*)(r0 + rl.cfree);
     rv.best = (int*)(r0 + rl.best);
+    rv.status = nullptr;
     rv.n_seeds = pl.B;
     rv.n = pl.n;
     rv.seed_base = s * pl.B;

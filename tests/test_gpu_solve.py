@@ -293,3 +293,24 @@ def test_tile_shapes_do_not_change_results_and_autotune():
     torch.cuda.synchronize()
     for a, b in zip(ref, out):
         assert torch.equal(a.traj, b.traj) and torch.equal(a.cost, b.cost)
+
+
+def test_status_word_reports_non_finite_seeds():
+    """The device status word of each problem: CR_ENAN (6) for a problem with
+    a NaN in one seed, CR_OK for the problem beside it, whose results are
+    those it has alone."""
+    rb, w, pr = scene(n_seeds=4, horizon=32)
+    R, W = crgb.Robot(rb), crgb.World(w)
+    bad = pr.seeds.copy()
+    bad[2, 5, 3] = np.nan
+    good = crgb.ProblemSpec(W, pr.q_start, pr.goal, 32, seeds=pr.seeds)
+    nan = crgb.ProblemSpec(W, pr.q_start, pr.goal, 32, seeds=bad)
+    ctx = crgb.Context(0)
+    og, on = crgb.solve(ctx, R, [good, nan], iters=5)
+    alone = crgb.solve(ctx, R, [good], iters=5)[0]
+    torch.cuda.synchronize()
+    assert int(og.status) == 0 and int(on.status) == 6
+    assert torch.equal(og.traj, alone.traj) and torch.equal(og.cost, alone.cost)
+    c = on.cost.cpu().numpy()
+    assert not np.isfinite(c[2]) and np.isfinite(c[[0, 1, 3]]).all()
+    assert int(on.best) != 2
