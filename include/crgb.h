@@ -40,10 +40,10 @@ typedef int32_t cr_status;
 #define CR_EINVAL 1    /* bad argument or size */
 #define CR_ENOMEM 2    /* device or host allocation failed */
 #define CR_ECUDA 3     /* a CUDA call failed (message has the CUDA error) */
-#define CR_ETIMEOUT 4  /* reserved: no call of this library waits on the device */
-#define CR_EBUSY 5     /* reserved: the server queues a request that does not fit yet */
-#define CR_ENAN 6      /* reserved: a non-finite cost is reported in the cost outputs (NaN never
-                          wins the best seed), not as a status */
+#define CR_ETIMEOUT 4  /* cr_server_wait: the request did not finish within the time limit */
+#define CR_EBUSY 5     /* cr_server_submit / cr_server_restore: the server's queue is full */
+#define CR_ENAN 6      /* device status word (cr_result.status, cr_server_poll): a seed's cost is
+                          not finite; NaN never wins the best seed */
 
 #define CR_MAX_DOF 16
 #define CR_MAX_ALPHA 16
@@ -400,38 +400,72 @@ cr_status cr_tune_set(cr_ctx* ctx, int32_t n_spheres, int32_t n_boxes, int32_t h
 /* ------------------------------------------------------------------------- */
 typedef struct cr_server cr_server;
 
-/* Request kinds: 0 = trajectory optimisation (motion generation), 1 = IK. */
+/* Request kinds: 0 = trajectory optimisation (motion generation), 1 = IK.
+ * A request brings its own seed count and horizon (IK: horizon 1); the kind
+ * fixes its parameters and iteration count.  Requests of one kind and one
+ * shape share a pool of device slots with its own stream. */
 typedef struct {
-  int32_t kind_seeds[2];      /* seeds per request of each kind */
-  int32_t kind_horizon[2];    /* horizon per request (IK: 1) */
-  int32_t kind_iters[2];      /* L-BFGS iterations per request, multiples of chunk */
-  cr_params kind_params[2];   /* parameters per kind (IK: CR_IK_MODE) */
-  int32_t chunk;              /* iterations each step runs for every active request */
-  int32_t max_active;         /* cap on active requests per kind (0 = memory decides) */
+  int32_t kind_iters[2];      /* L-BFGS iterations per request of each kind, multiples of chunk */
+  cr_params kind_params[2];   /* parameters per kind (kind 1 needs CR_IK_MODE) */
+  int32_t chunk;              /* iterations a pool runs per round for each of its active requests */
+  int32_t max_active;         /* cap on active requests per pool (0 = memory decides) */
   size_t reserve_bytes;       /* free device memory never given to request state */
+  int32_t max_queued;         /* submit / restore return CR_EBUSY while this many requests wait for a
+                                 slot (0 = no limit) */
 } cr_server_config;
 
 /* A server keeps the optimiser state of every active request on the device
- * (Sec. 4.1 state: iterate, gradient, history, candidates, best iterate). */
+ * (Sec. 4.1 state: iterate, gradient, history, candidates, best iterate).
+ * Not thread-safe: one host thread per server. */
 cr_status cr_server_create(cr_ctx* ctx, const cr_robot* robot, const cr_server_config* cfg,
                            cr_server** out);
+/* Waits for the server's running rounds, then frees it. */
 void cr_server_destroy(cr_server* server);
-/* Queue a request (host inputs copied; problem->seeds [B][H][dof] host).
- * It is admitted by a later step once a slot and free device memory allow. */
+/* Queue a request (host inputs copied; problem->seeds [B][H][dof] host,
+ * problem->goal_q optional).  It is admitted by a later step once a slot and
+ * free device memory allow.  CR_EBUSY (nothing queued) when max_queued
+ * requests already wait. */
 cr_status cr_server_submit(cr_server* server, int32_t kind, const cr_problem* problem,
                            uint64_t* ticket);
-/* One step: admit queued requests while free memory minus the reserve allows
- * (their initial evaluation and first L-BFGS step run), run `chunk`
- * iterations for every active request (one evaluation launch per kind over
- * all its requests' line-search candidates, one selection + L-BFGS launch;
- * the two kinds on two streams), retire finished requests.  Blocks until
- * the step's work is done.  Each request's result equals cr_solve of that
- * request alone with its kind's parameters and iterations. */
+/* One step; never waits for the device.  For every pool: if its last round
+ * has finished, the requests that retired in it become done (results already
+ * in pinned host memory) and their slots free; queued requests are admitted
+ * into free slots of idle pools (first come, first served per pool), a pool
+ * growing while free device memory minus the reserve allows; every idle pool
+ * with active requests starts a round: the initial evaluation and first
+ * L-BFGS step of its new requests, `chunk` iterations for all (one
+ * evaluation launch over all their line-search candidates, one selection +
+ * L-BFGS launch), the results of those reaching their iteration count copied
+ * to the host.  A request that arrives while its pool runs is admitted when
+ * that round ends; other pools are not held up.  Work follows `stream`.
+ * Each request's result equals cr_solve of that request alone with its
+ * kind's parameters and iterations, bit for bit. */
 cr_status cr_server_step(cr_server* server, void* stream);
 /* Results of a finished request into host buffers (any may be NULL):
- * traj [B][H][dof], cost [B], cfree [B], best seed index.  *done = 0 while pending. */
+ * traj [B][H][dof], cost [B], cfree [B], best seed index, device status word
+ * (CR_OK or CR_ENAN).  *done = 0 while pending. */
 cr_status cr_server_poll(cr_server* server, uint64_t ticket, int32_t* done, float* traj,
-                         float* cost, uint8_t* cfree, int32_t* best);
+                         float* cost, uint8_t* cfree, int32_t* best, int32_t* status);
+/* Step until the request is done; CR_ETIMEOUT after timeout_ms milliseconds
+ * (negative: no limit).  Blocks the host. */
+cr_status cr_server_wait(cr_server* server, uint64_t ticket, int32_t timeout_ms);
+/* Copy a pending request out of the server: its inputs and, once admitted,
+ * its whole device optimiser state (iterate, gradient, previous iterate and
+ * gradient, history ring, direction, line-search candidates, best iterate,
+ * iteration count) after its last round (waits for a running round; a
+ * request that finishes in it is no longer pending: CR_EINVAL).  With
+ * buf = NULL writes the size needed to *bytes; else *bytes is the buffer's
+ * size (CR_EINVAL, and the size needed, when too small).  The request keeps
+ * running in this server.  Host memory, opaque, valid for cr_server_restore
+ * on a server of the same robot and the same parameters for its kind. */
+cr_status cr_server_snapshot(cr_server* server, uint64_t ticket, void* buf, size_t* bytes);
+/* Queue a request from a snapshot (world: the handle of its world in this
+ * process).  Admitted like a new request, it continues from the saved state:
+ * its result is bit-identical to the original request's.  CR_EINVAL when the
+ * snapshot is malformed, of another robot, or of other parameters or
+ * iteration counts; CR_EBUSY as cr_server_submit. */
+cr_status cr_server_restore(cr_server* server, const void* buf, size_t bytes, const cr_world* world,
+                            uint64_t* ticket);
 /* Active and queued requests, device bytes held by request state. */
 cr_status cr_server_stats(cr_server* server, int32_t* active, int32_t* queued, size_t* pool_bytes);
 

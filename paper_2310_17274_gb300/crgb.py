@@ -29,7 +29,11 @@ _vp = C.c_void_p
 
 
 class CrError(RuntimeError):
-    pass
+    """A failed call; `status` is its cr_status code."""
+
+    def __init__(self, msg, status=1):
+        super().__init__(msg)
+        self.status = status
 
 
 class RobotDesc(C.Structure):
@@ -120,8 +124,11 @@ SIGNATURES = {
     "cr_server_destroy": ([_vp], None),
     "cr_server_submit": ([_vp, C.c_int32, C.POINTER(Problem), C.POINTER(C.c_uint64)], C.c_int32),
     "cr_server_step": ([_vp, _vp], C.c_int32),
-    "cr_server_poll": ([_vp, C.c_uint64, C.POINTER(C.c_int32), _vp, _vp, _vp, C.POINTER(C.c_int32)],
-                       C.c_int32),
+    "cr_server_poll": ([_vp, C.c_uint64, C.POINTER(C.c_int32), _vp, _vp, _vp, C.POINTER(C.c_int32),
+                        C.POINTER(C.c_int32)], C.c_int32),
+    "cr_server_wait": ([_vp, C.c_uint64, C.c_int32], C.c_int32),
+    "cr_server_snapshot": ([_vp, C.c_uint64, _vp, C.POINTER(C.c_size_t)], C.c_int32),
+    "cr_server_restore": ([_vp, _vp, C.c_size_t, _vp, C.POINTER(C.c_uint64)], C.c_int32),
     "cr_server_stats": ([_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_size_t)],
                         C.c_int32),
     "cr_eval_batch_noalloc": ([_vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), _ip, _vp, _vp,
@@ -150,7 +157,7 @@ def lib():
 def check(status: int, what: str = "") -> None:
     if status != 0:
         msg = lib().cr_last_error().decode()
-        raise CrError(f"{what} failed with status {status}: {msg}")
+        raise CrError(f"{what} failed with status {status}: {msg}", status)
 
 
 def _f32(a):
@@ -612,34 +619,32 @@ def tune_set(ctx: Context, n_spheres, n_boxes, horizon, block, short_tile, no_ca
 # ---------------------------------------------------------------------------
 
 class ServerConfig(C.Structure):
-    _fields_ = [("kind_seeds", C.c_int32 * 2), ("kind_horizon", C.c_int32 * 2),
-                ("kind_iters", C.c_int32 * 2), ("kind_params", Params * 2), ("chunk", C.c_int32),
-                ("max_active", C.c_int32), ("reserve_bytes", C.c_size_t)]
+    _fields_ = [("kind_iters", C.c_int32 * 2), ("kind_params", Params * 2), ("chunk", C.c_int32),
+                ("max_active", C.c_int32), ("reserve_bytes", C.c_size_t), ("max_queued", C.c_int32)]
 
 
 MG, IK = 0, 1
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENAN = 0, 1, 2, 3, 4, 5, 6
 
 
 class Server:
-    """Continuous-batching server (cr_server_*): requests of two kinds, state
-    resident on the device, admission by free device memory."""
+    """Continuous-batching server (cr_server_*): requests of two kinds and any
+    shape, state resident on the device, admission by free device memory."""
 
-    def __init__(self, ctx: Context, robot: Robot, mg=(32, 48, 100), ik=(32, 1, 50),
-                 mg_params=None, ik_params=None, chunk=10, max_active=0, reserve_bytes=2 << 30):
+    def __init__(self, ctx: Context, robot: Robot, mg_iters=100, ik_iters=50, mg_params=None, ik_params=None,
+                 chunk=10, max_active=0, reserve_bytes=2 << 30, max_queued=0):
         cfg = ServerConfig()
-        for k, (B, H, it) in enumerate((mg, ik)):
-            cfg.kind_seeds[k], cfg.kind_horizon[k], cfg.kind_iters[k] = B, H, it
+        cfg.kind_iters[0], cfg.kind_iters[1] = mg_iters, ik_iters
         cfg.kind_params[0] = mg_params if isinstance(mg_params, Params) else make_params(mg_params)
         ikp = ik_params if ik_params is not None else dict(flags=IK_MODE | SELF | WOLFE)
         cfg.kind_params[1] = ikp if isinstance(ikp, Params) else make_params(ikp)
-        cfg.chunk, cfg.max_active, cfg.reserve_bytes = chunk, max_active, reserve_bytes
-        self.shape = {MG: (mg[0], mg[1]), IK: (ik[0], ik[1])}
+        cfg.chunk, cfg.max_active, cfg.reserve_bytes, cfg.max_queued = chunk, max_active, reserve_bytes, max_queued
         self.dof = robot.dof
         h = _vp()
         check(lib().cr_server_create(ctx.handle, robot.handle, C.byref(cfg), C.byref(h)),
               "cr_server_create")
         self.handle = h
-        self._keep = {}
+        self._shape = {}
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -652,26 +657,44 @@ class Server:
         t = C.c_uint64()
         check(lib().cr_server_submit(self.handle, int(kind), C.byref(pr), C.byref(t)),
               "cr_server_submit")
-        self._keep[t.value] = kind
+        self._shape[t.value] = (int(pr.n_seeds), spec.horizon)
         return t.value
 
     def step(self, stream=None):
         check(lib().cr_server_step(self.handle, _stream(stream)), "cr_server_step")
 
     def poll(self, ticket):
-        """None while pending, else dict(traj, cost, cfree, best) (host numpy)."""
-        kind = self._keep[ticket]
-        B, H = self.shape[kind]
+        """None while pending, else dict(traj, cost, cfree, best, status) (host numpy)."""
+        B, H = self._shape[ticket]
         done = C.c_int32()
         traj = np.empty((B, H, self.dof), dtype=np.float32)
         cost = np.empty(B, dtype=np.float32)
         cfree = np.empty(B, dtype=np.uint8)
-        best = C.c_int32()
+        best, status = C.c_int32(), C.c_int32()
         check(lib().cr_server_poll(self.handle, int(ticket), C.byref(done), _p(traj), _p(cost),
-                                   _p(cfree, _up), C.byref(best)), "cr_server_poll")
+                                   _p(cfree, _up), C.byref(best), C.byref(status)), "cr_server_poll")
         if not done.value:
             return None
-        return dict(traj=traj, cost=cost, cfree=cfree.astype(bool), best=best.value)
+        return dict(traj=traj, cost=cost, cfree=cfree.astype(bool), best=best.value, status=status.value)
+
+    def wait(self, ticket, timeout_ms=-1):
+        check(lib().cr_server_wait(self.handle, int(ticket), int(timeout_ms)), "cr_server_wait")
+        return self.poll(ticket)
+
+    def snapshot(self, ticket) -> bytes:
+        n = C.c_size_t()
+        check(lib().cr_server_snapshot(self.handle, int(ticket), None, C.byref(n)), "cr_server_snapshot")
+        buf = C.create_string_buffer(n.value)
+        check(lib().cr_server_snapshot(self.handle, int(ticket), buf, C.byref(n)), "cr_server_snapshot")
+        return buf.raw[:n.value]
+
+    def restore(self, blob: bytes, world: World) -> int:
+        t = C.c_uint64()
+        buf = C.create_string_buffer(blob, len(blob))
+        check(lib().cr_server_restore(self.handle, buf, len(blob), world.handle, C.byref(t)), "cr_server_restore")
+        hdr = np.frombuffer(blob[:48], dtype=np.int32)
+        self._shape[t.value] = (int(hdr[3]), int(hdr[4]))   # B, H of the snapshot header
+        return t.value
 
     def stats(self):
         a, q, b = C.c_int32(), C.c_int32(), C.c_size_t()

@@ -141,8 +141,8 @@ def serving_benchmark(crgb, synth, ctx, R, rb, rates=(500.0, 100.0), seconds=3.0
     mg_p = crgb.make_params(dict(alpha=list(synth.ALPHA_8)))
     ik_p = crgb.make_params(dict(flags=crgb.IK_MODE | crgb.SELF | crgb.WOLFE))
     params = {crgb.MG: (mg_p, mg_iters), crgb.IK: (ik_p, ik_iters)}
-    server = crgb.Server(ctx, R, mg=(32, 48, mg_iters), ik=(32, 1, ik_iters), mg_params=mg_p,
-                         ik_params=ik_p, chunk=chunk)
+    server = crgb.Server(ctx, R, mg_iters=mg_iters, ik_iters=ik_iters, mg_params=mg_p, ik_params=ik_p,
+                         chunk=chunk)
     out = {"seconds": seconds, "drain_s": drain_s, "chunk": chunk, "mix": "MG:IK = 1:1",
            "mg_iters": mg_iters, "ik_iters": ik_iters, "rates": []}
     warmed = False
