@@ -62,6 +62,14 @@ typedef int32_t cr_status;
 #define CR_NO_SELF_CHECK 256u /* IK mode without CR_SELF: the collision-free flag leaves out self-collision
                                  (IK without collision checking, Sec. 6); EINVAL in any other mode */
 
+/* FP32 fused-multiply-add throughput of the current device (no counterpart
+ * in the paper: the peak the evaluation kernel's roofline is reported
+ * against).  Runs `iters` rounds of 128 independent FMAs per thread on a grid
+ * of resident CTAs covering every SM, timed with CUDA events on `stream`;
+ * writes TFLOP/s (an FMA counts as 2 FLOP) and the kernel time.  Synchronous;
+ * allocates a few KB of device memory. */
+cr_status cr_measure_ffma(int32_t iters, float* tflops, float* ms, void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* cr_last_error(void);
 /* Library version string. */

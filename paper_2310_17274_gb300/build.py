@@ -18,7 +18,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcrgb.so")
-SOURCES = ["k_eval.cu", "k_ik.cu", "k_opt.cu", "k_particle.cu", "k_steer.cu", "k_retime.cu", "k_rank.cu", "k_time.cu", "capi.cu", "runtime.cu", "server.cu", "noalloc.cu"]
+SOURCES = ["k_eval.cu", "k_ik.cu", "k_opt.cu", "k_particle.cu", "k_steer.cu", "k_retime.cu", "k_rank.cu", "k_time.cu", "capi.cu", "runtime.cu", "server.cu", "noalloc.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -93,6 +93,7 @@ SIGNATURES = {
     "cr_last_error": ([], C.c_char_p),
     "cr_version": ([], C.c_char_p),
     "cr_params_default": ([C.POINTER(Params)], None),
+    "cr_measure_ffma": ([C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), _vp], C.c_int32),
     "cr_robot_create": ([C.POINTER(RobotDesc), C.POINTER(_vp)], C.c_int32),
     "cr_robot_destroy": ([_vp], None),
     "cr_world_create": ([C.POINTER(WorldDesc), C.POINTER(_vp)], C.c_int32),
@@ -291,6 +292,13 @@ class ProblemSpec:
 # ---------------------------------------------------------------------------
 # hot-path calls
 # ---------------------------------------------------------------------------
+
+def measure_ffma(iters=400000, stream=None):
+    """FP32 FMA throughput of the current device (cr_measure_ffma): (TFLOP/s, ms)."""
+    t, ms = C.c_float(), C.c_float()
+    check(lib().cr_measure_ffma(int(iters), C.byref(t), C.byref(ms), _stream(stream)), "cr_measure_ffma")
+    return t.value, ms.value
+
 
 def fk(robot: Robot, theta, spheres=True, ee=True, link_tf=False, stream=None):
     """Forward kinematics of theta (CUDA tensor [N, dof])."""

@@ -131,8 +131,8 @@ def summarize(lat, arrivals, wall):
             "throughput_req_s": float(done.sum() / wall), "wall_s": float(wall)}
 
 
-def serving_benchmark(crgb, synth, ctx, R, rb, rates=(500.0, 100.0), seconds=3.0, warm_s=0.5,
-                      drain_s=10.0, chunk=10, mg_iters=100, ik_iters=50):
+def serving_benchmark(crgb, synth, ctx, R, rb, rates=(100.0, 250.0, 500.0), seconds=20.0, warm_s=2.0,
+                      drain_s=5.0, chunk=10, mg_iters=100, ik_iters=50, max_active=64):
     """Continuous batching vs plain per-request solves on the same Poisson
     stream (MG:IK = 1:1) at each rate.  Both paths see the same arrivals
     over warm_s + seconds and may drain for drain_s more; requests arriving
@@ -141,10 +141,13 @@ def serving_benchmark(crgb, synth, ctx, R, rb, rates=(500.0, 100.0), seconds=3.0
     mg_p = crgb.make_params(dict(alpha=list(synth.ALPHA_8)))
     ik_p = crgb.make_params(dict(flags=crgb.IK_MODE | crgb.SELF | crgb.WOLFE))
     params = {crgb.MG: (mg_p, mg_iters), crgb.IK: (ik_p, ik_iters)}
+    # at most max_active requests per pool: beyond the device's capacity the
+    # rest wait in the queue instead of slowing every round (and growing the
+    # pools) for all
     server = crgb.Server(ctx, R, mg_iters=mg_iters, ik_iters=ik_iters, mg_params=mg_p, ik_params=ik_p,
-                         chunk=chunk)
-    out = {"seconds": seconds, "drain_s": drain_s, "chunk": chunk, "mix": "MG:IK = 1:1",
-           "mg_iters": mg_iters, "ik_iters": ik_iters, "rates": []}
+                         chunk=chunk, max_active=max_active)
+    out = {"seconds": seconds, "warmup_s": warm_s, "drain_s": drain_s, "chunk": chunk, "mix": "MG:IK = 1:1",
+           "mg_iters": mg_iters, "ik_iters": ik_iters, "max_active_per_pool": max_active, "rates": []}
     warmed = False
     for k, rate in enumerate(rates):
         n = int(rate * (seconds + warm_s)) + 1
