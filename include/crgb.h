@@ -346,6 +346,29 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
                    const cr_params* params, int32_t iters, uint32_t solve_flags,
                    const cr_result* results, void* stream);
 
+/* cr_solve with particle-based optimisation of every seed first (Sec. 4.2,
+ * Eq. 12-13; App. B.3 runs 2 iterations before L-BFGS for IK and trajectory
+ * optimisation): each seed is the mean of its particles, sigma0 their
+ * initial variance; an iteration samples particles = mean + sqrt(variance) x
+ * eps, evaluates their cost (one launch over every particle of every
+ * problem) and updates mean and variance exactly as cr_particle_step does
+ * (bit for bit); the means then start the L-BFGS iterations.  eps (device)
+ * holds iters x n_particles x V zero-mean unit Gaussian samples (V = sum over
+ * problems of B_p H_p dof): for iteration k, problem after problem, the
+ * block [B_p][n_particles][H_p][dof] of cr_particle_step's layout.  The
+ * library draws no random numbers. */
+typedef struct {
+  int32_t iters;        /* particle iterations before L-BFGS */
+  int32_t n_particles;  /* particles per seed, 1..4096 */
+  float beta, k_mu, k_sigma;  /* as cr_particle_step */
+  float sigma0;         /* initial variance of every variable (>= 0) */
+  const float* eps;     /* device samples, see above */
+} cr_particle_config;
+
+cr_status cr_solve_particles(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
+                             const cr_params* params, int32_t iters, uint32_t solve_flags,
+                             const cr_particle_config* particles, const cr_result* results, void* stream);
+
 /* Alg. "Time Discretization" (App. "Time-step Discretization"): the
  * trajectory is first optimised at a coarse step without the jerk term, then
  * re-timed to the robot's limits and optimised again at that step.  Per

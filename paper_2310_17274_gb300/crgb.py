@@ -68,6 +68,11 @@ class Result(C.Structure):
     _fields_ = [("traj", _vp), ("cost", _vp), ("cfree", _vp), ("best", _vp), ("status", _vp)]
 
 
+class ParticleConfig(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("n_particles", C.c_int32), ("beta", C.c_float), ("k_mu", C.c_float),
+                ("k_sigma", C.c_float), ("sigma0", C.c_float), ("eps", _vp)]
+
+
 class TimeoptConfig(C.Structure):
     _fields_ = [("dt_init", C.c_float), ("dt_min", C.c_float), ("iters1", C.c_int32),
                 ("iters2", C.c_int32), ("w_pose", C.c_float), ("w_jerk", C.c_float), ("w_time", C.c_float)]
@@ -113,6 +118,8 @@ SIGNATURES = {
     "cr_retime": ([_vp, C.POINTER(Problem), C.c_int32, _vp, _vp, _vp], C.c_int32),
     "cr_rank_seeds": ([_vp, C.POINTER(Problem), C.POINTER(Params), C.c_int32, _vp, _vp, _vp, C.c_float,
                        C.c_float, C.c_float, C.c_float, _vp, _vp, _vp], C.c_int32),
+    "cr_solve_particles": ([_vp, _vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params), C.c_int32, C.c_uint32,
+                            C.POINTER(ParticleConfig), C.POINTER(Result), _vp], C.c_int32),
     "cr_solve_timeopt": ([_vp, _vp, C.c_int32, C.POINTER(Problem), C.POINTER(Params),
                           C.POINTER(TimeoptConfig), C.c_uint32, C.POINTER(Result), C.POINTER(TimeoptResult),
                           _vp], C.c_int32),
@@ -547,10 +554,13 @@ class SolveOutput:
 
 
 def solve(ctx: Context, robot: Robot, problems, params=None, iters=25, graph=True,
-          persistent=True, outputs=None, stream=None, device_seeds=None):
+          persistent=True, outputs=None, stream=None, device_seeds=None, particles=None):
     """Optimise a batch of problems (ProblemSpec with host seeds) together.
     With device_seeds (one CUDA tensor [B, H, dof] per problem) the seeds are
-    read from device memory instead.  Returns one SolveOutput per problem
+    read from device memory instead.  particles: dict(iters, n_particles,
+    beta, k_mu, k_sigma, sigma0, eps) runs particle-based optimisation of every
+    seed first (cr_solve_particles; eps a CUDA tensor of iters x n_particles x
+    V samples in that call's layout).  Returns one SolveOutput per problem
     (device tensors, valid once the stream has finished)."""
     probs = list(problems)
     n = len(probs)
@@ -568,8 +578,15 @@ def solve(ctx: Context, robot: Robot, problems, params=None, iters=25, graph=Tru
     flags = (SOLVE_GRAPH if graph else 0) | (SOLVE_PERSISTENT if persistent else 0)
     if device_seeds is not None:
         flags |= SOLVE_DEVICE_SEEDS
-    check(lib().cr_solve(ctx.handle, robot.handle, n, arr, C.byref(P), int(iters), flags, res,
-                         _stream(stream)), "cr_solve")
+    if particles is None:
+        check(lib().cr_solve(ctx.handle, robot.handle, n, arr, C.byref(P), int(iters), flags, res,
+                             _stream(stream)), "cr_solve")
+        return outputs
+    pc = ParticleConfig(int(particles["iters"]), int(particles["n_particles"]), float(particles["beta"]),
+                        float(particles["k_mu"]), float(particles["k_sigma"]), float(particles["sigma0"]),
+                        _dptr(particles["eps"].contiguous()))
+    check(lib().cr_solve_particles(ctx.handle, robot.handle, n, arr, C.byref(P), int(iters), flags, C.byref(pc),
+                                   res, _stream(stream)), "cr_solve_particles")
     return outputs
 
 

@@ -241,6 +241,12 @@ cudaError_t launch_eval_ik(const EvalArgs& a, cudaStream_t stream);
 int eval_ik_smem_bytes(int dof);
 int eval_ik_blocks_per_sm(int dof);
 cudaError_t launch_opt(const OptArgs& a, int n_max, cudaStream_t stream);
+// particle-based optimisation over the seeds of a batch (k_particle.cu):
+// phase 0 samples, phase 1 updates mean and covariance from the costs
+cudaError_t launch_particle_batch(const int4* seed_tab, int n_seeds, int n_p, int phase, const float* eps,
+                                  float* mu, float* sigma, float* particles, const float* cost, float beta,
+                                  float k_mu, float k_sigma, cudaStream_t s);
+cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t s);
 // time-discretised solve, between the two solves and after the second:
 // k_time.cu (one CTA per problem)
 cudaError_t launch_timeopt_mid(ProblemView* px, ProblemView* pc, int n_problems, const TimeoptView* tv,

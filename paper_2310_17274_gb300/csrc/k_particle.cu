@@ -25,17 +25,14 @@ __global__ void k_particle_sample(const float* __restrict__ mu, const float* __r
   }
 }
 
-// One CTA per seed.  Exponential utility of c = -cost / beta, taken after
-// subtracting the smallest cost (w unchanged); every thread forms the same
-// normaliser in particle order.  Then per variable, in particle order:
-// Eq. 12 mean and Eq. 13 covariance (weighted second moment about the
-// previous mean).
-__global__ void k_particle_update(const float* __restrict__ cost, const float* __restrict__ particles,
-                                  float* __restrict__ mu, float* __restrict__ sigma, int n, int n_p,
-                                  float inv_beta, float k_mu, float k_sigma) {
-  extern __shared__ float s_w[];  // [n_p]
-  const int b = blockIdx.x;
-  const float* c = cost + (long long)b * n_p;
+// UPDATE of one seed on one CTA: exponential utility of c = -cost / beta,
+// taken after subtracting the smallest cost (w unchanged); every thread forms
+// the same normaliser in particle order.  Then per variable, in particle
+// order: Eq. 12 mean and Eq. 13 covariance (weighted second moment about the
+// previous mean).  c [n_p] costs, th [n_p][n] particles, mu / sigma [n].
+__device__ __forceinline__ void particle_update_seed(const float* c, const float* th, float* mu, float* sigma,
+                                                     int n, int n_p, float inv_beta, float k_mu, float k_sigma,
+                                                     float* s_w) {
   float cmin = c[0];
   for (int i = 1; i < n_p; ++i) cmin = fminf(cmin, c[i]);
   for (int i = threadIdx.x; i < n_p; i += blockDim.x) s_w[i] = expf(-(c[i] - cmin) * inv_beta);
@@ -43,10 +40,8 @@ __global__ void k_particle_update(const float* __restrict__ cost, const float* _
   float z = 0.f;
   for (int i = 0; i < n_p; ++i) z += s_w[i];
   const float inv_z = 1.f / z;
-  const float* th = particles + (long long)b * n_p * n;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const long long v = (long long)b * n + k;
-    const float m0 = mu[v];
+    const float m0 = mu[k];
     float m = 0.f, s2 = 0.f;
     for (int i = 0; i < n_p; ++i) {
       const float w = s_w[i] * inv_z;
@@ -55,12 +50,73 @@ __global__ void k_particle_update(const float* __restrict__ cost, const float* _
       const float d = t - m0;
       s2 = fmaf(w, d * d, s2);
     }
-    sigma[v] = fmaf(1.f - k_sigma, sigma[v], k_sigma * s2);
-    mu[v] = fmaf(1.f - k_mu, m0, k_mu * m);
+    sigma[k] = fmaf(1.f - k_sigma, sigma[k], k_sigma * s2);
+    mu[k] = fmaf(1.f - k_mu, m0, k_mu * m);
   }
 }
 
+// One CTA per seed of one problem.
+__global__ void k_particle_update(const float* __restrict__ cost, const float* __restrict__ particles,
+                                  float* __restrict__ mu, float* __restrict__ sigma, int n, int n_p,
+                                  float inv_beta, float k_mu, float k_sigma) {
+  extern __shared__ float s_w[];  // [n_p]
+  const int b = blockIdx.x;
+  particle_update_seed(cost + (long long)b * n_p, particles + (long long)b * n_p * n, mu + (long long)b * n,
+                       sigma + (long long)b * n, n, n_p, inv_beta, k_mu, k_sigma, s_w);
+}
+
+// The seeds of a batch of uneven problems (seed table rows: n variables,
+// variable offset, seed index, problem): particles and samples of seed s at
+// n_p x its variable offset, its costs at n_p x its index.
+__global__ void k_particle_sample_tab(const int4* __restrict__ seed_tab, const float* __restrict__ mu,
+                                      const float* __restrict__ sigma, const float* __restrict__ eps,
+                                      float* __restrict__ particles, int n_p) {
+  const int4 e = seed_tab[blockIdx.x];
+  const int n = e.x;
+  const long long vo = e.y;
+  for (int q = threadIdx.x; q < n_p * n; q += blockDim.x) {
+    const int k = q % n;
+    const long long at = vo * n_p + q;
+    particles[at] = fmaf(sqrtf(sigma[vo + k]), eps[at], mu[vo + k]);
+  }
+}
+
+__global__ void k_particle_update_tab(const int4* __restrict__ seed_tab, const float* __restrict__ cost,
+                                      const float* __restrict__ particles, float* __restrict__ mu,
+                                      float* __restrict__ sigma, int n_p, float inv_beta, float k_mu,
+                                      float k_sigma) {
+  extern __shared__ float s_w[];  // [n_p]
+  const int4 e = seed_tab[blockIdx.x];
+  const long long vo = e.y;
+  particle_update_seed(cost + (long long)e.z * n_p, particles + vo * n_p, mu + vo, sigma + vo, e.x, n_p,
+                       inv_beta, k_mu, k_sigma, s_w);
+}
+
+__global__ void k_fill(float* __restrict__ p, long long n, float v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
 }  // namespace
+
+cudaError_t launch_particle_batch(const int4* seed_tab, int n_seeds, int n_p, int phase, const float* eps,
+                                  float* mu, float* sigma, float* particles, const float* cost, float beta,
+                                  float k_mu, float k_sigma, cudaStream_t s) {
+  if (n_seeds <= 0) return cudaSuccess;
+  if (phase == 0)
+    k_particle_sample_tab<<<n_seeds, 256, 0, s>>>(seed_tab, mu, sigma, eps, particles, n_p);
+  else
+    k_particle_update_tab<<<n_seeds, 256, (size_t)n_p * sizeof(float), s>>>(seed_tab, cost, particles, mu, sigma,
+                                                                            n_p, 1.f / beta, k_mu, k_sigma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long want = (n + 255) / 256;
+  k_fill<<<(int)(want < 152 * 8 ? want : 152 * 8), 256, 0, s>>>(p, n, v);
+  return cudaGetLastError();
+}
 
 }  // namespace crgb
 

@@ -121,16 +121,23 @@ struct Plan {
   int P = 0, S = 0, dof = 0, m = 0, na = 0;
   long long V = 0;
   int n_max = 0;
-  std::vector<ProblemView> probs_x, probs_c;
-  std::vector<int4> tiles_x, tiles_c, seedtab;
+  std::vector<ProblemView> probs_x, probs_c, probs_p;
+  std::vector<int4> tiles_x, tiles_c, tiles_p, seedtab;
+  int max_traj_p = 0, max_states_p = 0, n_part = 0;
   std::vector<ResultView> results;
   int max_traj_x = 0, max_states_x = 0, max_traj_c = 0, max_states_c = 0, max_h = 0;
   int block = kEvalBlock;
   int no_store_x = 0;
   // workspace offsets (bytes)
   size_t o_x, o_g, o_xp, o_gp, o_dir, o_bx, o_c, o_bc, o_rho, o_it, o_s, o_y, o_cand, o_cgrad,
-      o_ccost, o_cfree, o_bfree, o_ls, o_queue, o_tdt, o_tsc, ws_bytes;
-  size_t o_tx, o_tc, o_px, o_pc, o_seed, o_res, o_tv, tab_bytes;
+      o_ccost, o_cfree, o_bfree, o_ls, o_queue, o_tdt, o_tsc, o_sig, o_part, o_pcost, ws_bytes;
+  size_t o_tx, o_tc, o_px, o_pc, o_seed, o_res, o_tv, o_tp, o_pp, tab_bytes;
+};
+
+// Particle-based optimisation of every seed before L-BFGS (Sec. 4.2, App.
+// B.3: two iterations for IK and trajectory optimisation).
+struct ParticlePlan {
+  cr_particle_config cfg;
 };
 
 // A time-discretised solve (Alg. "Time Discretization"): two solves with the
@@ -188,8 +195,10 @@ int4 tuned(const cr_ctx* ctx, int M, int K, int H) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* pr,
-                     const cr_params* prm, const cr_result* res, const TimeoptPlan* to, Plan& pl) {
+                     const cr_params* prm, const cr_result* res, const TimeoptPlan* to,
+                     const ParticlePlan* pp, Plan& pl) {
   pl.P = P;
+  pl.n_part = pp ? pp->cfg.n_particles : 0;
   pl.dof = rb->dof;
   pl.m = prm->history;
   pl.na = prm->n_alpha;
@@ -216,6 +225,13 @@ cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* p
     pc.traj_base = sb * pl.na;
     pc.var_base = vo * pl.na;
     pl.probs_c[p] = pc;
+    if (pl.n_part > 0) {  // the particles of every seed, [B][n_particles][n] per problem
+      ProblemView pq = pv;
+      pq.n_traj = B * pl.n_part;
+      pq.traj_base = sb * pl.n_part;
+      pq.var_base = vo * pl.n_part;
+      pl.probs_p.push_back(pq);
+    }
     for (int b = 0; b < B; ++b) pl.seedtab.push_back(make_int4(n, (int)(vo + (long long)b * n), sb + b, p));
     ResultView rv;
     rv.traj = res ? res[p].traj : nullptr;
@@ -261,6 +277,10 @@ cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* p
   };
   make_tiles(pl.probs_x, pl.tiles_x, pl.max_traj_x, pl.max_states_x);
   make_tiles(pl.probs_c, pl.tiles_c, pl.max_traj_c, pl.max_states_c);
+  if (pl.n_part > 0) {
+    if (pl.V * pl.n_part > (1ll << 31) - 1) return failf(CR_EINVAL, "batch too large for its particles");
+    make_tiles(pl.probs_p, pl.tiles_p, pl.max_traj_p, pl.max_states_p);
+  }
   // workspace
   const size_t V = (size_t)pl.V, S = (size_t)pl.S, m = pl.m, na = pl.na;
   size_t o = 0;
@@ -272,6 +292,8 @@ cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* p
   pl.o_ccost = take(S * na * 4); pl.o_cfree = take(S * na); pl.o_bfree = take(S);
   pl.o_ls = take(S * 4); pl.o_queue = take(256);
   pl.o_tdt = take(to ? S * 4 : 0); pl.o_tsc = take(to ? S * 4 : 0);
+  const size_t np = (size_t)pl.n_part;
+  pl.o_sig = take(np ? V * 4 : 0); pl.o_part = take(V * np * 4); pl.o_pcost = take(S * np * 4);
   pl.ws_bytes = o;
   o = 0;
   pl.o_tx = take(pl.tiles_x.size() * sizeof(int4));
@@ -281,6 +303,8 @@ cr_status build_plan(cr_ctx* ctx, const cr_robot* rb, int P, const cr_problem* p
   pl.o_seed = take(pl.seedtab.size() * sizeof(int4));
   pl.o_res = take(P * sizeof(ResultView));
   pl.o_tv = take(to ? P * sizeof(TimeoptView) : 0);
+  pl.o_tp = take(pl.tiles_p.size() * sizeof(int4));
+  pl.o_pp = take(pl.probs_p.size() * sizeof(ProblemView));
   pl.tab_bytes = o;
   if (ctx->mem_budget && pl.ws_bytes + pl.tab_bytes > ctx->mem_budget)
     return failf(CR_ENOMEM, "batch needs %zu bytes > context budget %zu", pl.ws_bytes + pl.tab_bytes,
@@ -318,7 +342,7 @@ cr_opt_state state_of(const Plan& pl, unsigned char* ws) {
 // the per-problem results are written at the end.
 cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* prm, const Plan& pl,
                              unsigned char* ws, unsigned char* tab, int iters, bool persistent,
-                             cudaStream_t s, bool finish = true) {
+                             cudaStream_t s, bool finish = true, const ParticlePlan* pp = nullptr) {
   const cr_opt_state st = state_of(pl, ws);
   int* queue = (int*)(ws + pl.o_queue);
   auto eval_args = [&](bool cand) {
@@ -373,6 +397,48 @@ cr_status enqueue_iterations(cr_ctx* ctx, const cr_robot* rb, const cr_params* p
   o.st = st;
   o.reset_queue = persistent ? queue : nullptr;
 
+  // particle-based optimisation (Sec. 4.2) moves every seed first: the seeds
+  // are the means, sigma0 the initial variance; per iteration the samples,
+  // their costs (one evaluation launch over every particle of every problem,
+  // no gradients) and the update of mean and variance
+  if (pp && pp->cfg.iters > 0) {
+    const cr_particle_config& c = pp->cfg;
+    float* sigma = (float*)(ws + pl.o_sig);
+    float* part = (float*)(ws + pl.o_part);
+    float* pcost = (float*)(ws + pl.o_pcost);
+    const int4* seeds = (const int4*)(tab + pl.o_seed);
+    RT_CUDA(launch_fill(sigma, pl.V, c.sigma0, s));
+    for (int k = 0; k < c.iters; ++k) {
+      const float* eps = c.eps + (size_t)k * c.n_particles * pl.V;
+      RT_CUDA(launch_particle_batch(seeds, pl.S, c.n_particles, 0, eps, st.x, sigma, part, nullptr, c.beta, c.k_mu,
+                                    c.k_sigma, s));
+      EvalArgs a{};
+      std::memset(&a, 0, sizeof(a));
+      a.rb = rb->view;
+      a.prm = *prm;
+      a.problems = (const ProblemView*)(tab + pl.o_pp);
+      a.tiles = (const int4*)(tab + pl.o_tp);
+      a.n_tiles = (int)pl.tiles_p.size();
+      a.max_traj = pl.max_traj_p;
+      a.max_states = pl.max_states_p;
+      a.max_horizon = pl.max_h;
+      a.theta = part;
+      a.cost = pcost;
+      a.no_store_x = pl.no_store_x;
+      const int smem = eval_smem_bytes(a, pl.block);
+      if (smem > eval_smem_limit()) return failf(CR_EINVAL, "particle tile needs %d bytes of shared memory", smem);
+      int grid = a.n_tiles;
+      const int per_sm = std::max(1, eval_blocks_per_sm(a, pl.block));
+      if (a.n_tiles > per_sm * ctx->n_sm) {
+        grid = per_sm * ctx->n_sm;
+        a.queue = queue;
+        RT_CUDA(cudaMemsetAsync(queue, 0, sizeof(int), s));
+      }
+      RT_CUDA(launch_eval(a, grid, pl.block, s));
+      RT_CUDA(launch_particle_batch(seeds, pl.S, c.n_particles, 1, nullptr, st.x, sigma, part, pcost, c.beta,
+                                    c.k_mu, c.k_sigma, s));
+    }
+  }
   // iteration state starts empty
   RT_CUDA(cudaMemsetAsync(st.s, 0, (size_t)pl.V * pl.m * 4, s));
   RT_CUDA(cudaMemsetAsync(st.y, 0, (size_t)pl.V * pl.m * 4, s));
@@ -420,11 +486,13 @@ cr_status enqueue_timeopt(cr_ctx* ctx, const cr_robot* rb, const cr_params* prm,
 }
 
 std::string graph_key(const cr_robot* rb, const cr_params* prm, const Plan& pl, int iters,
-                      bool persistent, const void* ws, const void* tab, int block, const TimeoptPlan* to) {
+                      bool persistent, const void* ws, const void* tab, int block, const TimeoptPlan* to,
+                      const ParticlePlan* pp) {
   std::string k;
   auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
-  const int kind = to ? 1 : 0;
+  const int kind = (to ? 1 : 0) | (pp ? 2 : 0);
   put(&kind, sizeof(kind));
+  if (pp) put(&pp->cfg, sizeof(pp->cfg));  // the samples' address included
   if (to) {
     put(&to->sc, sizeof(to->sc));
     put(&to->iters1, sizeof(int));
@@ -480,7 +548,7 @@ namespace {
 // The body of cr_solve and cr_solve_timeopt (to != nullptr).
 cr_status solve_impl(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
                      const cr_params* params, int32_t iters, uint32_t solve_flags, const cr_result* results,
-                     void* stream, const TimeoptPlan* to) {
+                     void* stream, const TimeoptPlan* to, const ParticlePlan* pp = nullptr) {
   if (!ctx || !robot || !problems || n_problems < 1) return failf(CR_EINVAL, "cr_solve: bad argument");
   if (iters < 0) return failf(CR_EINVAL, "cr_solve: iters < 0");
   cr_status s = check_params(params);
@@ -488,7 +556,7 @@ cr_status solve_impl(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, con
   for (int p = 0; p < n_problems; ++p)
     if (!problems[p].seeds) return failf(CR_EINVAL, "problem %d: null seeds", p);
   Plan pl;
-  s = build_plan(ctx, robot, n_problems, problems, params, results, to, pl);
+  s = build_plan(ctx, robot, n_problems, problems, params, results, to, pp, pl);
   if (s != CR_OK) return s;
   if (opt_smem_bytes(params->history, pl.n_max) > 200 * 1024)
     return failf(CR_EINVAL, "history * horizon * dof too large for shared memory");
@@ -530,6 +598,8 @@ cr_status solve_impl(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, con
   std::memcpy(h + pl.o_seed, pl.seedtab.data(), pl.seedtab.size() * sizeof(int4));
   std::memcpy(h + pl.o_res, pl.results.data(), pl.P * sizeof(ResultView));
   if (to) std::memcpy(h + pl.o_tv, to->views.data(), pl.P * sizeof(TimeoptView));
+  if (!pl.tiles_p.empty()) std::memcpy(h + pl.o_tp, pl.tiles_p.data(), pl.tiles_p.size() * sizeof(int4));
+  if (!pl.probs_p.empty()) std::memcpy(h + pl.o_pp, pl.probs_p.data(), pl.probs_p.size() * sizeof(ProblemView));
   RT_CUDA(cudaMemcpyAsync(tab, h, pl.tab_bytes, cudaMemcpyHostToDevice, st));
   // seeds -> x (host memory, or device memory with CR_SOLVE_DEVICE_SEEDS)
   if (host_seeds) {
@@ -549,10 +619,10 @@ cr_status solve_impl(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, con
   const bool persistent = (solve_flags & CR_SOLVE_PERSISTENT) != 0;
   auto enqueue = [&](cudaStream_t q) {
     return to ? enqueue_timeopt(ctx, robot, params, pl, *to, ws, tab, persistent, q)
-              : enqueue_iterations(ctx, robot, params, pl, ws, tab, iters, persistent, q);
+              : enqueue_iterations(ctx, robot, params, pl, ws, tab, iters, persistent, q, true, pp);
   };
   if (!(solve_flags & CR_SOLVE_GRAPH)) return enqueue(st);
-  const std::string key = graph_key(robot, params, pl, iters, persistent, ws, tab, pl.block, to);
+  const std::string key = graph_key(robot, params, pl, iters, persistent, ws, tab, pl.block, to, pp);
   cudaGraphExec_t exec = nullptr;
   for (auto& g : ctx->graphs)
     if (g.first == key) exec = g.second;
@@ -593,6 +663,22 @@ cr_status cr_solve(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const
                    const cr_params* params, int32_t iters, uint32_t solve_flags,
                    const cr_result* results, void* stream) {
   return solve_impl(ctx, robot, n_problems, problems, params, iters, solve_flags, results, stream, nullptr);
+}
+
+cr_status cr_solve_particles(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,
+                             const cr_params* params, int32_t iters, uint32_t solve_flags,
+                             const cr_particle_config* particles, const cr_result* results, void* stream) {
+  if (!particles) return failf(CR_EINVAL, "cr_solve_particles: null particle configuration");
+  const cr_particle_config& c = *particles;
+  if (c.iters < 0 || c.n_particles < 1 || c.n_particles > 4096)
+    return failf(CR_EINVAL, "cr_solve_particles: iters < 0 or n_particles outside 1..4096");
+  if (!(c.beta > 0.f) || !(c.k_mu >= 0.f && c.k_mu <= 1.f) || !(c.k_sigma >= 0.f && c.k_sigma <= 1.f) ||
+      !(c.sigma0 >= 0.f))
+    return failf(CR_EINVAL, "cr_solve_particles: beta must be > 0, k_mu and k_sigma in [0, 1], sigma0 >= 0");
+  if (c.iters > 0 && !c.eps) return failf(CR_EINVAL, "cr_solve_particles: null samples");
+  ParticlePlan pp;
+  pp.cfg = c;
+  return solve_impl(ctx, robot, n_problems, problems, params, iters, solve_flags, results, stream, nullptr, &pp);
 }
 
 cr_status cr_solve_timeopt(cr_ctx* ctx, const cr_robot* robot, int32_t n_problems, const cr_problem* problems,

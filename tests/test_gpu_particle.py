@@ -112,3 +112,53 @@ def test_particle_step_rejects_bad_arguments():
     for kw in (dict(beta=0.0), dict(beta=1.0, k_mu=1.5), dict(beta=1.0, k_sigma=-0.1)):
         with pytest.raises(crgb.CrError):
             crgb.particle_step(R, spec, mu, _dev(np.ones_like(pr.seeds)), eps, **kw)
+
+
+@pytest.mark.parametrize("ik", [False, True])
+def test_particles_in_solve_equal_particle_steps(ik):
+    """cr_solve_particles: particle iterations over every seed of a batch of
+    uneven problems, then L-BFGS, equal bit for bit to cr_particle_step on
+    each problem followed by cr_solve from the resulting means (trajectory
+    problems of horizons 32 and 20; IK problems of 32 and 12 seeds)."""
+    rb = scene(spheres=synth.SPHERES_60)[0]
+    R = crgb.Robot(rb)
+    ctx = crgb.Context(0)
+    shapes = [(12, 32, 1), (20, 12, 1)] if ik else [(10, 4, 32), (25, 3, 20)]
+    specs, keep, probs = [], [], []
+    for k, (K, B, H) in enumerate(shapes):
+        _, w, pr = scene(spheres=synth.SPHERES_60, n_boxes=K, n_seeds=B, horizon=max(H, 2), world_seed=70 + k,
+                         problem_seed=80 + k)
+        seeds = pr.seeds[:, :H].copy() if H > 1 else f32(synth.uniform_config(np.random.default_rng(k), rb, B))[:, None]
+        W = crgb.World(w)
+        keep.append(W)
+        specs.append(crgb.ProblemSpec(W, pr.q_start, pr.goal, H, seeds=seeds))
+        probs.append((W, pr, seeds))
+    p = dict(flags=crgb.IK_MODE | crgb.SELF | crgb.WOLFE) if ik else None
+    n_p, iters_p = 8, 2
+    V = sum(sd.size for _, _, sd in probs)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    eps = torch.randn(iters_p * n_p * V, device="cuda", generator=g)
+    cfg = dict(iters=iters_p, n_particles=n_p, beta=1000.0, k_mu=0.9, k_sigma=0.9, sigma0=0.01, eps=eps)
+    out = crgb.solve(ctx, R, specs, p, iters=5, particles=cfg)
+    out0 = crgb.solve(ctx, R, specs, p, iters=0, particles=cfg)
+    torch.cuda.synchronize()
+    # the same particle iterations problem by problem
+    means = []
+    off = 0
+    for (W, pr, sd), spec in zip(probs, specs):
+        B, H, D = sd.shape
+        mu = torch.tensor(sd, dtype=torch.float32, device="cuda").contiguous()
+        sigma = torch.full_like(mu, 0.01)
+        for k in range(iters_p):
+            e = eps[k * n_p * V + off * n_p: k * n_p * V + (off + sd.size) * n_p].view(B, n_p, H, D)
+            crgb.particle_step(R, crgb.ProblemSpec(W, pr.q_start, pr.goal, H), mu, sigma, e.contiguous(), p,
+                               beta=1000.0, k_mu=0.9, k_sigma=0.9)
+        means.append(mu)
+        off += sd.size
+    ref = crgb.solve(ctx, R, specs, p, iters=5, device_seeds=means)
+    torch.cuda.synchronize()
+    for a, b, m in zip(out, ref, means):
+        for k in ("traj", "cost", "cfree", "best", "status"):
+            assert torch.equal(getattr(a, k), getattr(b, k)), k
+    for a, m in zip(out0, means):   # no L-BFGS iteration: the means themselves
+        assert torch.equal(a.traj, m)
