@@ -493,6 +493,7 @@ def main():
                                     "what": "same solve, eager launches, no CUDA graph"}
     if rank == 0 and "ik" in want:
         extras["ik"] = bench_ik(crgb, synth, ctx, R, rb)
+        extras["ik_particles"] = bench_ik(crgb, synth, ctx, R, rb, particle_iters=2)
         extras["ik_no_collision"] = bench_ik(crgb, synth, ctx, R, rb, collision=False)
     if rank == 0 and "particle" in want:
         extras["particle"] = bench_particle(crgb, synth, ctx, R, rb, world, pr, P, iters)
@@ -537,7 +538,8 @@ def main():
     return 0
 
 
-def bench_ik(crgb, synth, ctx, R, rb, n_goals=1000, n_seeds=32, iters=50, collision=True):
+def bench_ik(crgb, synth, ctx, R, rb, n_goals=1000, n_seeds=32, iters=50, collision=True, particle_iters=0,
+             n_particles=16, sigma0=0.01):
     """Batched IK: 1000 goals x 32 seeds (H = 1) in one solve.  With
     collision: 40 cuboids, self-collision on, goals from FK of collision-free
     configurations; without: no cuboids, no self term and no self check in
@@ -581,15 +583,26 @@ def bench_ik(crgb, synth, ctx, R, rb, n_goals=1000, n_seeds=32, iters=50, collis
     seeds = synth.uniform_config(rng, rb, n_goals * n_seeds).reshape(n_goals, n_seeds, 1, rb.dof)
     specs = [crgb.ProblemSpec(W, qs, goals[g], 1, seeds=seeds[g]) for g in range(n_goals)]
     choice = crgb.autotune(ctx, R, specs, ikp, iters=5)
+    # particle iterations before L-BFGS (App. B.3), from unit Gaussian samples
+    # drawn on the device with a fixed generator seed
+    pcfg = None
+    if particle_iters > 0:
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(321)
+        eps = torch.randn(particle_iters * n_particles * n_goals * n_seeds * rb.dof, device="cuda", generator=gen)
+        pcfg = dict(iters=particle_iters, n_particles=n_particles, beta=1000.0, k_mu=0.9, k_sigma=0.9,
+                    sigma0=sigma0, eps=eps)
     outs = None
     for _ in range(3):
-        outs = crgb.solve(ctx, R, specs, ikp, iters=iters, graph=True, persistent=True, outputs=outs)
+        outs = crgb.solve(ctx, R, specs, ikp, iters=iters, graph=True, persistent=True, outputs=outs,
+                          particles=pcfg)
     torch.cuda.synchronize()
     ts = []
     for _ in range(5):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        outs = crgb.solve(ctx, R, specs, ikp, iters=iters, graph=True, persistent=True, outputs=outs)
+        outs = crgb.solve(ctx, R, specs, ikp, iters=iters, graph=True, persistent=True, outputs=outs,
+                          particles=pcfg)
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1) / 1e3)
@@ -640,6 +653,9 @@ def bench_ik(crgb, synth, ctx, R, rb, n_goals=1000, n_seeds=32, iters=50, collis
             "evals_per_s": n_goals * n_seeds * (iters * ikp.n_alpha + 1) / t,
             "goals_from": "FK of configurations sampled within the limits"
                           + (" (collision-free)" if collision else ""),
+            "particle_iters": particle_iters,
+            "particles": (f"{n_particles} per seed, sigma0 {sigma0}, beta 1000, k_mu = k_sigma = 0.9, "
+                          "unit Gaussian samples") if particle_iters else None,
             "autotune": choice}
 
 
@@ -667,18 +683,15 @@ def bench_particle(crgb, synth, ctx, R, rb, world, pr, P, iters, n_particles=16,
     gen.manual_seed(123)
     ramp = torch.arange(1, H + 1, device="cuda", dtype=torch.float32).view(1, 1, 1, H, 1) / H
     eps = (torch.randn((n_iters, B, n_particles, 1, D), device="cuda", generator=gen) * ramp).contiguous()
-    seeds0 = torch.tensor(pr.seeds, dtype=torch.float32, device="cuda")
+    eps = eps.expand(n_iters, B, n_particles, H, D).contiguous()
     sspec = crgb.ProblemSpec(W, pr.q_start, pr.goal, H, seeds=pr.seeds)
+    cfg = dict(iters=n_iters, n_particles=n_particles, beta=beta, k_mu=k_mu, k_sigma=k_sigma, sigma0=sigma0,
+               eps=eps)
 
     def run(particles):
-        mu = seeds0.clone()
-        if particles:
-            sg = torch.full_like(mu, sigma0)
-            for k in range(n_iters):
-                crgb.particle_step(R, spec, mu, sg, eps[k], params=P, beta=beta, k_mu=k_mu,
-                                   k_sigma=k_sigma)
+        # one graph-captured cr_solve_particles call: particle iterations, then L-BFGS
         return crgb.solve(ctx, R, [sspec], P, iters=iters, graph=True, persistent=True,
-                          device_seeds=[mu])[0]
+                          particles=cfg if particles else None)[0]
 
     out = {}
     for particles in (False, True):
