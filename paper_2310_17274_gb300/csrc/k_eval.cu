@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include "crgb_internal.cuh"
+#include "fastdiv.h"
 #include "k_device.cuh"
 
 namespace crgb {
@@ -60,6 +61,9 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   __shared__ int s_nlist;
   __shared__ int s_nll;
   __shared__ int s_nbw;
+  // invariant divisors of the work-item indices: joints, spheres, link-pair
+  // groups, spheres per link (per CTA); horizon, stencil samples (per tile)
+  __shared__ FastDiv s_fdD, s_fdM, s_fdG, s_fdL, s_fdH, s_fdNS;
 
   const int D = a.rb.dof, M = a.rb.n_spheres, P = a.rb.n_pairs, G = a.rb.n_groups;
   const int GW = (G + 31) / 32;
@@ -139,6 +143,12 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   for (int k = tid; k < P; k += nthr) s_pairs[k] = a.rb.pairs[k];
   for (int k = tid; k < G; k += nthr) s_grp[k] = a.rb.groups[k];
   for (int k = tid; k < D; k += nthr) s_axis[k] = a.rb.axis[k];
+  if (tid == 0) {
+    s_fdD = make_fastdiv(D);
+    s_fdM = make_fastdiv(M);
+    s_fdG = make_fastdiv(G);
+    s_fdL = make_fastdiv(a.rb.max_link_spheres);
+  }
   // the robot is constant; trajectories, the work counter and the outputs
   // belong to the previous grid until it has finished
   pdl_wait();
@@ -184,6 +194,10 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     const long long vbase = s_prob.var_base + (long long)r0 * H * D;
 
     for (int k = tid; k < S * D; k += nthr) s_th[k] = a.theta[vbase + k];
+    if (tid == 0) {
+      s_fdH = make_fastdiv(H);
+      s_fdNS = make_fastdiv((H + 1) * D);
+    }
     for (int k = tid; k < nt; k += nthr) {
       s_free[k] = 1;
       s_goal[k] = 0.f;
@@ -195,7 +209,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     __syncthreads();
     // joint sines and cosines of every slot, all threads at once
     for (int k = tid; k < (1 + S) * D; k += nthr) {
-      const int s = k / D, j = k % D;
+      const int s = fdiv(k, s_fdD), j = k - s * D;
       float sn, cs;
       sincosf(s == 0 ? s_prob.q_start[j] : s_th[(s - 1) * D + j], &sn, &cs);
       s_sc[k] = make_float2(sn, cs);
@@ -229,7 +243,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     };
     if (store_x) {
       for (int k = tid; k < (1 + S) * M; k += nthr) {
-        const int sl = k / M, i = k % M;
+        const int sl = fdiv(k, s_fdM), i = k - sl * M;
         const V3 x = sphere_at(sl, i);
         s_x[k] = make_float4(x.x, x.y, x.z, s_sph[i].w);
       }
@@ -240,8 +254,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     // most |dc| + |dR|_F d to a neighbouring state, so half of that bounds the
     // sweep length L of each of its spheres, and reach = R_link + max(eta, L).
     for (int k = tid; k < S * D; k += nthr) {
-      const int sg = k / D, l = k % D;
-      const int r = sg / H, t = sg % H + 1;
+      const int sg = fdiv(k, s_fdD), l = k - sg * D;
+      const int r = fdiv(sg, s_fdH), t = sg - r * H + 1;
       const float4 lb = s_lbs[l];
       const float* T1 = s_lt + (slot(r, t) * D + l) * 12;
       const V3 c = tf_point(T1, lb.x, lb.y, lb.z);
@@ -357,7 +371,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     // pair search below skips the others); the world term's first barrier
     // publishes the mask.
     for (int k = tid; k < S * G; k += nthr) {
-      const int sg = k / G, g = k % G;
+      const int sg = fdiv(k, s_fdG), g = k - sg * G;
       const int4 gr = s_grp[g];
       const float4 A = s_rho[sg * D + gr.x], B = s_rho[sg * D + gr.y];
       const float ra = s_lbs[gr.x].w, rb = s_lbs[gr.y].w;
@@ -414,10 +428,10 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
         __syncthreads();
         // (2) the sweep of a (state, sphere) over the boxes in mask m, in box order
         auto sweep_item = [&](int k, unsigned long long m) {
-          const int sg = k / M, i = k % M;
-          const int r = sg / H;
+          const int sg = fdiv(k, s_fdM), i = k - sg * M;
+          const int r = fdiv(sg, s_fdH);
           const float rad = s_sph[i].w;
-          const SphereMotion mo = motion(r, sg % H + 1, i);
+          const SphereMotion mo = motion(r, sg - r * H + 1, i);
           const V3 x1 = mo.x1;
           float4 acc4 = s_sg[k];
           bool clear = true;
@@ -472,19 +486,20 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
         //      them densely
         const int n_ll = s_nll, spl = a.rb.max_link_spheres;
         for (int w = tid; w < n_ll * spl; w += nthr) {
-          const int sl0 = s_llist[w / spl], jl = w % spl;
-          const int sg = sl0 / D, l = sl0 % D;
+          const int wl = fdiv(w, s_fdL);
+          const int sl0 = s_llist[wl], jl = w - wl * spl;
+          const int sg = fdiv(sl0, s_fdD), l = sl0 - sg * D;
           if (jl >= s_lst[l + 1] - s_lst[l]) continue;
           const int i = s_lsp[s_lst[l] + jl];
           const int k = sg * M + i;
           const float rad = s_sph[i].w;
           if (rad < 0.f) continue;
           unsigned long long m0 = (unsigned long long)s_mask[2 * sl0] | ((unsigned long long)s_mask[2 * sl0 + 1] << 32);
-          const int r = sg / H;
+          const int r = fdiv(sg, s_fdH);
           // boxes within the link-level bound of this sphere's reach first
           unsigned long long m = 0ull;
           {
-            const V3 xp = pos(slot(r, sg % H + 1), i);
+            const V3 xp = pos(slot(r, sg - r * H + 1), i);
             const float tu = rad + s_lm[sg * D + s_link[i]];
             while (m0) {
               const int kk = __ffsll((long long)m0) - 1;
@@ -524,7 +539,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     // than 1 mm apart were skipped above; the rest are searched pair by pair,
     // a warp per state
     for (int sg = warp; sg < S; sg += nw) {
-      const int r = sg / H, t = sg % H + 1;
+      const int r = fdiv(sg, s_fdH), t = sg - r * H + 1;
       const int sl = slot(r, t);
       const float4* X = store_x ? s_x + sl * M : s_wsph + warp * M;
       if (!store_x) {
@@ -593,8 +608,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     //     the neighbouring waypoints) and the self term; it replaces the sweep
     //     gradient in place (the sum S stays for the neighbours)
     auto bw1_item = [&](int k) {
-      const int sg = k / M, i = k % M;
-      const int r = sg / H, t = sg % H + 1;
+      const int sg = fdiv(k, s_fdM), i = k - sg * M;
+      const int r = fdiv(sg, s_fdH), t = sg - r * H + 1;
       const float4 c = s_sph[i];
       float wc = 0.f;
       V3 gx = v3(0.f, 0.f, 0.f);
@@ -654,8 +669,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     // (1a) list the (state, sphere) items whose gradient can be non-zero:
     //      nothing reaches the others, their gradient and cost stay zero
     for (int k = tid; k < S * M; k += nthr) {
-      const int sg = k / M, i = k % M;
-      const int t = sg % H + 1;
+      const int sg = fdiv(k, s_fdM), i = k - sg * M;
+      const int t = sg - fdiv(sg, s_fdH) * H + 1;
       const int parg0 = selfc ? s_sta[sg] : -1;
       bool in_pair = false;
       if (parg0 >= 0) {
@@ -689,8 +704,9 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     //      link centres and box masks (unused since the collision terms)
     float* s_pf = reinterpret_cast<float*>(smem + L.off_rho);  // [S][dof][6]
     for (int k = tid; k < S * D; k += nthr) {
-      const int sg = k / D, l = k % D;
-      const int sl = slot(sg / H, sg % H + 1);
+      const int sg = fdiv(k, s_fdD), l = k - sg * D;
+      const int rr = fdiv(sg, s_fdH);
+      const int sl = slot(rr, sg - rr * H + 1);
       V3 P = v3(0.f, 0.f, 0.f), F = v3(0.f, 0.f, 0.f);
       for (int q = s_lst[l]; q < s_lst[l + 1]; ++q) {
         const int i = s_lsp[q];
@@ -708,7 +724,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     // ---- Eq. 17 position bound; App. A.5 stencils with Eq. 16 and Eq. 17 on v, a, j
     const int NS = H + 1;
     for (int k = tid; k < S * D; k += nthr) {
-      const int j = k % D;
+      const int j = k - fdiv(k, s_fdD) * D;
       float sl;
       s_pb[k] = prm.w_bound * bound_cost(s_th[k], s_lim[j], s_lim[D + j], e2, inv_e2, sl);
     }
@@ -722,7 +738,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
                 inv2dt3 = 1.f / (2.f * dt * dt * dt);
     if (!ik) {
       for (int k = tid; k < nt * NS * D; k += nthr) {
-        const int r = k / (NS * D), rem = k % (NS * D), e = rem / D + 2, j = rem % D;
+        const int r = fdiv(k, s_fdNS), rem = k - r * (NS * D), e0 = fdiv(rem, s_fdD), e = e0 + 2, j = rem - e0 * D;
         const float qm2 = ext(r, e - 2, j), qm1 = ext(r, e - 1, j), q0 = ext(r, e, j),
                     qp1 = ext(r, e + 1, j), qp2 = ext(r, e + 2, j);
         const float vel = (qm2 - 8.f * qm1 + 8.f * qp1 - qp2) * inv12dt;
@@ -753,8 +769,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     // (2b) per (state, joint): the suffix sums and the end-effector terms; the
     //      joint-0 item also adds up the state's world cost in sphere order
     for (int k = tid; k < S * D; k += nthr) {
-      const int sg = k / D, j = k % D;
-      const int r = sg / H, t = sg % H + 1;
+      const int sg = fdiv(k, s_fdD), j = k - sg * D;
+      const int r = fdiv(sg, s_fdH), t = sg - r * H + 1;
       const int sl = slot(r, t);
       const float* T = s_lt + (sl * D + j) * 12;
       const int ax = s_axis[j];
@@ -792,7 +808,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
 
     // ---- gradient: kinematic part + position bound + stencil transpose
     for (int k = tid; k < S * D; k += nthr) {
-      const int sg = k / D, j = k % D, r = sg / H, t = sg % H + 1;
+      const int sg = fdiv(k, s_fdD), j = k - sg * D, r = fdiv(sg, s_fdH), t = sg - r * H + 1;
       float sl;
       bound_cost(s_th[k], s_lim[j], s_lim[D + j], e2, inv_e2, sl);
       float g = s_gth[k] + prm.w_bound * sl;
