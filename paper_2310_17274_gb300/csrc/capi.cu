@@ -245,6 +245,11 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
   r->view.link_start = reinterpret_cast<const int*>(b + o_lst);
   r->view.link_sph = reinterpret_cast<const int*>(b + o_lsp);
   r->view.max_link_spheres = max_ls;
+  r->view.fd_dof = make_fastdiv(D);
+  r->view.fd_sph = make_fastdiv(M);
+  r->view.fd_grp = make_fastdiv(G);
+  r->view.fd_lsph = make_fastdiv(max_ls);
+  r->view.fd_sphw = make_fastdiv((M + 31) / 32);
   r->view.pair_at = n_at > 0 ? reinterpret_cast<const int16_t*>(b + o_pat) : nullptr;
   r->view.link_sph4 = reinterpret_cast<const float4*>(b + o_ls4);
   for (int j = 0; j < D; ++j) {
@@ -346,6 +351,8 @@ cr_status fill_problem(const cr_robot* rb, const cr_problem* pr, ProblemView* pv
   pv->boxes = pr->world->dev;
   pv->n_boxes = pr->world->n;
   pv->horizon = pr->horizon;
+  pv->fd_h = make_fastdiv(pr->horizon);
+  pv->fd_hd = make_fastdiv((pr->horizon + 1) * rb->dof);
   for (int j = 0; j < rb->dof; ++j) pv->q_start[j] = pr->q_start[j];
   for (int a = 0; a < 3; ++a) pv->goal_p[a] = pr->goal[a];
   double R[9];

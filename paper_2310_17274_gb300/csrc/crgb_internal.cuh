@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "../../include/crgb.h"
+#include "fastdiv.h"
 
 namespace crgb {
 
@@ -65,6 +66,9 @@ struct RobotView {
   int max_link_spheres;     // largest sphere count of a link
   const int16_t* pair_at;   // [M][M] grouped index of the pair {i, j} (caller's first when listed
                             //   twice) or -1; robots of up to kPairTableSpheres spheres, else nullptr
+  // dividers of work-item indices (set on the host): dof, spheres, link-pair
+  // groups, largest sphere count of a link, 32-bit words of a sphere mask
+  FastDiv fd_dof, fd_sph, fd_grp, fd_lsph, fd_sphw;
 };
 
 // One box packed as five float4 rows: (R^T row k, t_k) for k = 0..2 so that
@@ -91,6 +95,9 @@ struct ProblemView {
   // problem (the parameters' values, or those a time-discretised solve sets
   // on the device between its two solves)
   float dt, w_vel, w_acc, w_jerk;
+  // dividers of work-item indices (set on the host): horizon, stencil
+  // samples of a trajectory times dof ((horizon + 1) dof)
+  FastDiv fd_h, fd_hd;
 };
 
 // Arguments of the fused evaluation kernel.
@@ -156,7 +163,11 @@ struct EvalSmem {
     off_stw = take(max_states * 4);
     off_sts = take(max_states * 4);
     off_sta = take(max_states * 4);
-    off_gth = take(max_states * dof * 4);
+    {  // joint gradients of the backward pass; before it, one bit per
+       // (state, sphere) marking the items whose gradient can be non-zero
+      const int mw = (M + 31) / 32;
+      off_gth = take(max_states * (dof > mw ? dof : mw) * 4);
+    }
     {  // per-warp sphere positions of the self term (without the cache), then
        // the world cost of each (state, sphere) in backward passes 1-2
       const int wsph = store_x ? 0 : n_warps * M * 16, wc = max_states * M * 4;

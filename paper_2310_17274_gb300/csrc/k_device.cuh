@@ -90,6 +90,50 @@ __device__ __forceinline__ void fk_chain(const float* fix, const int* axis, int 
   }
 }
 
+// One row of the serial chain: row r of T_j = (row r of T_{j-1}) F_j J(theta_j)
+// depends on row r alone, so three threads can run a chain together.  The
+// same operations as fk_joint / fk_chain for that row (bit-identical); writes
+// row r of T_0..T_{dof-1} into out (12 floats per joint).
+__device__ __forceinline__ void fk_chain_row(const float* fix, const int* axis, int dof, const float2* sc,
+                                             int row, float* out) {
+  float t0 = row == 0 ? 1.f : 0.f, t1 = row == 1 ? 1.f : 0.f, t2 = row == 2 ? 1.f : 0.f, t3 = 0.f;
+  for (int j = 0; j < dof; ++j) {
+    const float s = sc[j].x, c = sc[j].y;
+    const float* F = fix + 12 * j;
+    const int ax = axis[j];
+    float A[12];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float f0 = F[4 * r], f1 = F[4 * r + 1], f2 = F[4 * r + 2];
+      if (ax == 0) {
+        A[4 * r] = f0;
+        A[4 * r + 1] = fmaf(f1, c, f2 * s);
+        A[4 * r + 2] = fmaf(-f1, s, f2 * c);
+      } else if (ax == 1) {
+        A[4 * r] = fmaf(f0, c, -f2 * s);
+        A[4 * r + 1] = f1;
+        A[4 * r + 2] = fmaf(f0, s, f2 * c);
+      } else {
+        A[4 * r] = fmaf(f0, c, f1 * s);
+        A[4 * r + 1] = fmaf(-f0, s, f1 * c);
+        A[4 * r + 2] = f2;
+      }
+      A[4 * r + 3] = F[4 * r + 3];
+    }
+    float n[4];
+#pragma unroll
+    for (int col = 0; col < 4; ++col) {
+      const float v = fmaf(t0, A[col], fmaf(t1, A[4 + col], t2 * A[8 + col]));
+      n[col] = col == 3 ? v + t3 : v;
+    }
+    t0 = n[0];
+    t1 = n[1];
+    t2 = n[2];
+    t3 = n[3];
+    *reinterpret_cast<float4*>(out + 12 * j + 4 * row) = make_float4(t0, t1, t2, t3);
+  }
+}
+
 // Box signed distance in the box frame (textbook: Euclidean outside, minus
 // the smallest face gap inside) and its gradient in the box frame; inside,
 // the face of the largest q wins, lowest axis on ties.

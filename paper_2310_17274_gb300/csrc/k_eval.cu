@@ -21,7 +21,6 @@
 #include <math.h>
 
 #include "crgb_internal.cuh"
-#include "fastdiv.h"
 #include "k_device.cuh"
 
 namespace crgb {
@@ -61,9 +60,6 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   __shared__ int s_nlist;
   __shared__ int s_nll;
   __shared__ int s_nbw;
-  // invariant divisors of the work-item indices: joints, spheres, link-pair
-  // groups, spheres per link (per CTA); horizon, stencil samples (per tile)
-  __shared__ FastDiv s_fdD, s_fdM, s_fdG, s_fdL, s_fdH, s_fdNS;
 
   const int D = a.rb.dof, M = a.rb.n_spheres, P = a.rb.n_pairs, G = a.rb.n_groups;
   const int GW = (G + 31) / 32;
@@ -111,6 +107,9 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   // region once the self term no longer needs it
   float* s_wc = reinterpret_cast<float*>(smem + L.off_wsph);
   float* s_gth = reinterpret_cast<float*>(smem + L.off_gth);
+  // until the backward pass: the (state, sphere) items whose gradient can be
+  // non-zero, one bit each, set by the sweep and the self term
+  uint32_t* s_bwm = reinterpret_cast<uint32_t*>(smem + L.off_gth);
   BoxRows* s_box = reinterpret_cast<BoxRows*>(smem + L.off_box);
   float4* s_ee = reinterpret_cast<float4*>(smem + L.off_ee);
   float* s_sten = reinterpret_cast<float*>(smem + L.off_sten);
@@ -143,12 +142,6 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
   for (int k = tid; k < P; k += nthr) s_pairs[k] = a.rb.pairs[k];
   for (int k = tid; k < G; k += nthr) s_grp[k] = a.rb.groups[k];
   for (int k = tid; k < D; k += nthr) s_axis[k] = a.rb.axis[k];
-  if (tid == 0) {
-    s_fdD = make_fastdiv(D);
-    s_fdM = make_fastdiv(M);
-    s_fdG = make_fastdiv(G);
-    s_fdL = make_fastdiv(a.rb.max_link_spheres);
-  }
   // the robot is constant; trajectories, the work counter and the outputs
   // belong to the previous grid until it has finished
   pdl_wait();
@@ -194,10 +187,6 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     const long long vbase = s_prob.var_base + (long long)r0 * H * D;
 
     for (int k = tid; k < S * D; k += nthr) s_th[k] = a.theta[vbase + k];
-    if (tid == 0) {
-      s_fdH = make_fastdiv(H);
-      s_fdNS = make_fastdiv((H + 1) * D);
-    }
     for (int k = tid; k < nt; k += nthr) {
       s_free[k] = 1;
       s_goal[k] = 0.f;
@@ -205,21 +194,25 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     for (int k = tid; k < S * M; k += nthr) s_sg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int k = tid; k < S * GW; k += nthr) s_gmask[k] = 0u;
     if (tid == 0) s_nbw = 0;
-    for (int k = tid; k < S * MW; k += nthr) s_nz[k] = 0u;
+    for (int k = tid; k < S * MW; k += nthr) {
+      s_nz[k] = 0u;
+      s_bwm[k] = 0u;
+    }
     __syncthreads();
     // joint sines and cosines of every slot, all threads at once
     for (int k = tid; k < (1 + S) * D; k += nthr) {
-      const int s = fdiv(k, s_fdD), j = k - s * D;
+      const int s = fdiv(k, a.rb.fd_dof), j = k - s * D;
       float sn, cs;
       sincosf(s == 0 ? s_prob.q_start[j] : s_th[(s - 1) * D + j], &sn, &cs);
       s_sc[k] = make_float2(sn, cs);
     }
     __syncthreads();
 
-    // ---- forward kinematics: slot 0 = start state, slot 1 + sigma = state sigma
-    for (int s = tid; s < 1 + S; s += nthr) {
-      const float* q = s == 0 ? s_prob.q_start : s_th + (s - 1) * D;
-      fk_chain(s_fix, s_axis, D, q, s_sc + s * D, s_lt + s * D * 12);
+    // ---- forward kinematics: slot 0 = start state, slot 1 + sigma = state
+    // sigma; three threads per slot, one row of the transforms each
+    for (int k = tid; k < 3 * (1 + S); k += nthr) {
+      const int s = k / 3;
+      fk_chain_row(s_fix, s_axis, D, s_sc + s * D, k - 3 * s, s_lt + s * D * 12);
     }
     __syncthreads();
 
@@ -243,7 +236,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     };
     if (store_x) {
       for (int k = tid; k < (1 + S) * M; k += nthr) {
-        const int sl = fdiv(k, s_fdM), i = k - sl * M;
+        const int sl = fdiv(k, a.rb.fd_sph), i = k - sl * M;
         const V3 x = sphere_at(sl, i);
         s_x[k] = make_float4(x.x, x.y, x.z, s_sph[i].w);
       }
@@ -254,8 +247,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     // most |dc| + |dR|_F d to a neighbouring state, so half of that bounds the
     // sweep length L of each of its spheres, and reach = R_link + max(eta, L).
     for (int k = tid; k < S * D; k += nthr) {
-      const int sg = fdiv(k, s_fdD), l = k - sg * D;
-      const int r = fdiv(sg, s_fdH), t = sg - r * H + 1;
+      const int sg = fdiv(k, a.rb.fd_dof), l = k - sg * D;
+      const int r = fdiv(sg, s_prob.fd_h), t = sg - r * H + 1;
       const float4 lb = s_lbs[l];
       const float* T1 = s_lt + (slot(r, t) * D + l) * 12;
       const V3 c = tf_point(T1, lb.x, lb.y, lb.z);
@@ -371,7 +364,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     // pair search below skips the others); the world term's first barrier
     // publishes the mask.
     for (int k = tid; k < S * G; k += nthr) {
-      const int sg = fdiv(k, s_fdG), g = k - sg * G;
+      const int sg = fdiv(k, a.rb.fd_grp), g = k - sg * G;
       const int4 gr = s_grp[g];
       const float4 A = s_rho[sg * D + gr.x], B = s_rho[sg * D + gr.y];
       const float ra = s_lbs[gr.x].w, rb = s_lbs[gr.y].w;
@@ -428,10 +421,10 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
         __syncthreads();
         // (2) the sweep of a (state, sphere) over the boxes in mask m, in box order
         auto sweep_item = [&](int k, unsigned long long m) {
-          const int sg = fdiv(k, s_fdM), i = k - sg * M;
-          const int r = fdiv(sg, s_fdH);
+          const int sg = fdiv(k, a.rb.fd_sph), i = k - sg * M;
+          const int r = fdiv(sg, s_prob.fd_h), t = sg - r * H + 1;
           const float rad = s_sph[i].w;
-          const SphereMotion mo = motion(r, sg - r * H + 1, i);
+          const SphereMotion mo = motion(r, t, i);
           const V3 x1 = mo.x1;
           float4 acc4 = s_sg[k];
           bool clear = true;
@@ -479,6 +472,15 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
           }
           s_sg[k] = acc4;
           if (!clear) s_free[r] = 0;
+          // the item's gradient, and through the speed its neighbours', can be
+          // non-zero (S only grows over box chunks, so the marks cover the end state)
+          const uint32_t bit = 1u << (i & 31);
+          const int wi = i >> 5;
+          if (acc4.x != 0.f || acc4.y != 0.f || acc4.z != 0.f || acc4.w != 0.f) atomicOr(&s_bwm[sg * MW + wi], bit);
+          if (speed && acc4.x != 0.f) {
+            if (t >= 2) atomicOr(&s_bwm[(sg - 1) * MW + wi], bit);
+            if (t + 1 <= H) atomicOr(&s_bwm[(sg + 1) * MW + wi], bit);
+          }
         };
         // (2a) per sphere of a listed (state, link): the boxes of the link's mask
         //      within the link-level bound of the sphere; the few items with any
@@ -486,16 +488,16 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
         //      them densely
         const int n_ll = s_nll, spl = a.rb.max_link_spheres;
         for (int w = tid; w < n_ll * spl; w += nthr) {
-          const int wl = fdiv(w, s_fdL);
+          const int wl = fdiv(w, a.rb.fd_lsph);
           const int sl0 = s_llist[wl], jl = w - wl * spl;
-          const int sg = fdiv(sl0, s_fdD), l = sl0 - sg * D;
+          const int sg = fdiv(sl0, a.rb.fd_dof), l = sl0 - sg * D;
           if (jl >= s_lst[l + 1] - s_lst[l]) continue;
           const int i = s_lsp[s_lst[l] + jl];
           const int k = sg * M + i;
           const float rad = s_sph[i].w;
           if (rad < 0.f) continue;
           unsigned long long m0 = (unsigned long long)s_mask[2 * sl0] | ((unsigned long long)s_mask[2 * sl0 + 1] << 32);
-          const int r = fdiv(sg, s_fdH);
+          const int r = fdiv(sg, s_prob.fd_h);
           // boxes within the link-level bound of this sphere's reach first
           unsigned long long m = 0ull;
           {
@@ -539,7 +541,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     // than 1 mm apart were skipped above; the rest are searched pair by pair,
     // a warp per state
     for (int sg = warp; sg < S; sg += nw) {
-      const int r = fdiv(sg, s_fdH), t = sg - r * H + 1;
+      const int r = fdiv(sg, s_prob.fd_h), t = sg - r * H + 1;
       const int sl = slot(r, t);
       const float4* X = store_x ? s_x + sl * M : s_wsph + warp * M;
       if (!store_x) {
@@ -550,7 +552,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
         __syncwarp();
       }
       // deepest penetration and its pair; the caller's pair index (ties: the
-      // first pair in the caller's list) is fetched only for exact ties
+      // first pair in the caller's list) is fetched only for exact ties.  A
+      // lane takes up to three pairs of a group at once (independent loads).
       float best = 0.f;
       int arg = -1;
       bool touch = false;
@@ -560,41 +563,60 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
           const int g = w * 32 + __ffs(gm) - 1;
           gm &= gm - 1u;
           const int4 gr = s_grp[g];
-#pragma unroll 4
-          for (int p = gr.z + lane; p < gr.z + gr.w; p += 32) {
-            const uint32_t pr = s_pairs[p];
-            const float4 A = X[pr & 0xffffu], B = X[pr >> 16];
-            const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
-            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float rs = A.w + B.w;
-            const float lim = rs + 1e-3f;
-            // disabled spheres, or separated by more than 1 mm: no effect
-            if (A.w <= 0.f || B.w <= 0.f || d2 >= lim * lim) continue;
-            const float pen = rs - sqrtf(d2);
-            if (!(-pen > 0.f)) touch = true;
-            if (pen > best) {
-              best = pen;
-              arg = p;
-            } else if (pen == best && pen > 0.f && a.rb.pair_orig[p] < a.rb.pair_orig[arg]) {
-              arg = p;  // exact tie: first in the caller's list
+          const int end = gr.z + gr.w;
+          for (int p0 = gr.z + lane; p0 < end; p0 += 96) {
+            uint32_t pr[3];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) pr[u] = p0 + 32 * u < end ? s_pairs[p0 + 32 * u] : 0u;
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+              const int p = p0 + 32 * u;
+              const float4 A = X[pr[u] & 0xffffu], B = X[pr[u] >> 16];
+              const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
+              const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              const float rs = A.w + B.w;
+              const float lim = rs + 1e-3f;
+              // past the group, disabled spheres, or separated by more than
+              // 1 mm: no effect
+              if (p >= end || A.w <= 0.f || B.w <= 0.f || d2 >= lim * lim) continue;
+              const float pen = rs - sqrtf(d2);
+              if (!(-pen > 0.f)) touch = true;
+              if (pen > best) {
+                best = pen;
+                arg = p;
+              } else if (pen == best && pen > 0.f && a.rb.pair_orig[p] < a.rb.pair_orig[arg]) {
+                arg = p;  // exact tie: first in the caller's list
+              }
             }
           }
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
-        if (ob > best || (ob == best && ob > 0.f && oa != arg && a.rb.pair_orig[oa] < a.rb.pair_orig[arg])) {
-          best = ob;
-          arg = oa;
+      // across lanes: the largest penetration (best >= 0, so its bits order
+      // as integers), ties to the first pair in the caller's list
+      const float bmax = __int_as_float(__reduce_max_sync(0xffffffffu, __float_as_int(best)));
+      int barg = -1;
+      if (bmax > 0.f) {
+        const bool cand = best == bmax;
+        const uint32_t cm = __ballot_sync(0xffffffffu, cand);
+        if (__popc(cm) == 1) {
+          barg = __shfl_sync(0xffffffffu, arg, __ffs(cm) - 1);
+        } else {
+          const int ori = cand ? a.rb.pair_orig[arg] : 0x7fffffff;
+          const int omin = __reduce_min_sync(0xffffffffu, ori);
+          barg = __shfl_sync(0xffffffffu, arg, __ffs(__ballot_sync(0xffffffffu, cand && ori == omin)) - 1);
         }
       }
       touch = __any_sync(0xffffffffu, touch);
       if (lane == 0) {
-        s_sts[sg] = best;
-        s_sta[sg] = arg;
+        s_sts[sg] = bmax;
+        s_sta[sg] = barg;
         if (touch) s_free[r] = 0;
+        if (selfc && barg >= 0) {  // the deepest pair's spheres carry the self gradient
+          const uint32_t pr = s_pairs[barg];
+          const int pi = (int)(pr & 0xffffu), pj = (int)(pr >> 16);
+          atomicOr(&s_bwm[sg * MW + (pi >> 5)], 1u << (pi & 31));
+          atomicOr(&s_bwm[sg * MW + (pj >> 5)], 1u << (pj & 31));
+        }
       }
       __syncwarp();
     }
@@ -608,8 +630,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     //     the neighbouring waypoints) and the self term; it replaces the sweep
     //     gradient in place (the sum S stays for the neighbours)
     auto bw1_item = [&](int k) {
-      const int sg = fdiv(k, s_fdM), i = k - sg * M;
-      const int r = fdiv(sg, s_fdH), t = sg - r * H + 1;
+      const int sg = fdiv(k, a.rb.fd_sph), i = k - sg * M;
+      const int r = fdiv(sg, s_prob.fd_h), t = sg - r * H + 1;
       const float4 c = s_sph[i];
       float wc = 0.f;
       V3 gx = v3(0.f, 0.f, 0.f);
@@ -666,28 +688,24 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
       if (wc != 0.f || gx.x != 0.f || gx.y != 0.f || gx.z != 0.f)
         atomicOr(&s_nz[sg * MW + i / 32], 1u << (i % 32));
     };
-    // (1a) list the (state, sphere) items whose gradient can be non-zero:
+    // (1a) list the (state, sphere) items whose gradient can be non-zero
+    //      (marked by the sweep and the self term: own sweep result, a
+    //      neighbour's sweep sum through the speed, the deepest self pair);
     //      nothing reaches the others, their gradient and cost stay zero
-    for (int k = tid; k < S * M; k += nthr) {
-      const int sg = fdiv(k, s_fdM), i = k - sg * M;
-      const int t = sg - fdiv(sg, s_fdH) * H + 1;
-      const int parg0 = selfc ? s_sta[sg] : -1;
-      bool in_pair = false;
-      if (parg0 >= 0) {
-        const uint32_t pr = s_pairs[parg0];
-        in_pair = i == (int)(pr & 0xffffu) || i == (int)(pr >> 16);
+    for (int w = tid; w < S * MW; w += nthr) {
+      uint32_t bits = s_bwm[w];
+      if (!bits) continue;
+      const int sg = fdiv(w, a.rb.fd_sphw), i0 = (w - sg * MW) * 32;
+      int e = atomicAdd(&s_nbw, __popc(bits));
+      while (bits) {
+        const int k = sg * M + i0 + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        if (e < bw_cap)
+          s_list[e] = (uint32_t)k;
+        else
+          bw1_item(k);
+        ++e;
       }
-      const float4 own = s_sg[k];
-      const float Sm0 = (speed && t >= 2) ? s_sg[k - M].x : 0.f;
-      const float Sp0 = (speed && t + 1 <= H) ? s_sg[k + M].x : 0.f;
-      if (!in_pair && own.x == 0.f && own.y == 0.f && own.z == 0.f && own.w == 0.f && Sm0 == 0.f &&
-          Sp0 == 0.f)
-        continue;
-      const int e = atomicAdd(&s_nbw, 1);
-      if (e < bw_cap)
-        s_list[e] = (uint32_t)k;
-      else
-        bw1_item(k);
     }
     __syncthreads();
     // (1b) the listed items, any thread
@@ -704,8 +722,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     //      link centres and box masks (unused since the collision terms)
     float* s_pf = reinterpret_cast<float*>(smem + L.off_rho);  // [S][dof][6]
     for (int k = tid; k < S * D; k += nthr) {
-      const int sg = fdiv(k, s_fdD), l = k - sg * D;
-      const int rr = fdiv(sg, s_fdH);
+      const int sg = fdiv(k, a.rb.fd_dof), l = k - sg * D;
+      const int rr = fdiv(sg, s_prob.fd_h);
       const int sl = slot(rr, sg - rr * H + 1);
       V3 P = v3(0.f, 0.f, 0.f), F = v3(0.f, 0.f, 0.f);
       for (int q = s_lst[l]; q < s_lst[l + 1]; ++q) {
@@ -724,7 +742,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     // ---- Eq. 17 position bound; App. A.5 stencils with Eq. 16 and Eq. 17 on v, a, j
     const int NS = H + 1;
     for (int k = tid; k < S * D; k += nthr) {
-      const int j = k - fdiv(k, s_fdD) * D;
+      const int j = k - fdiv(k, a.rb.fd_dof) * D;
       float sl;
       s_pb[k] = prm.w_bound * bound_cost(s_th[k], s_lim[j], s_lim[D + j], e2, inv_e2, sl);
     }
@@ -738,7 +756,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
                 inv2dt3 = 1.f / (2.f * dt * dt * dt);
     if (!ik) {
       for (int k = tid; k < nt * NS * D; k += nthr) {
-        const int r = fdiv(k, s_fdNS), rem = k - r * (NS * D), e0 = fdiv(rem, s_fdD), e = e0 + 2, j = rem - e0 * D;
+        const int r = fdiv(k, s_prob.fd_hd), rem = k - r * (NS * D), e0 = fdiv(rem, a.rb.fd_dof), e = e0 + 2, j = rem - e0 * D;
         const float qm2 = ext(r, e - 2, j), qm1 = ext(r, e - 1, j), q0 = ext(r, e, j),
                     qp1 = ext(r, e + 1, j), qp2 = ext(r, e + 2, j);
         const float vel = (qm2 - 8.f * qm1 + 8.f * qp1 - qp2) * inv12dt;
@@ -769,8 +787,8 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     // (2b) per (state, joint): the suffix sums and the end-effector terms; the
     //      joint-0 item also adds up the state's world cost in sphere order
     for (int k = tid; k < S * D; k += nthr) {
-      const int sg = fdiv(k, s_fdD), j = k - sg * D;
-      const int r = fdiv(sg, s_fdH), t = sg - r * H + 1;
+      const int sg = fdiv(k, a.rb.fd_dof), j = k - sg * D;
+      const int r = fdiv(sg, s_prob.fd_h), t = sg - r * H + 1;
       const int sl = slot(r, t);
       const float* T = s_lt + (sl * D + j) * 12;
       const int ax = s_axis[j];
@@ -808,7 +826,7 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
 
     // ---- gradient: kinematic part + position bound + stencil transpose
     for (int k = tid; k < S * D; k += nthr) {
-      const int sg = fdiv(k, s_fdD), j = k - sg * D, r = fdiv(sg, s_fdH), t = sg - r * H + 1;
+      const int sg = fdiv(k, a.rb.fd_dof), j = k - sg * D, r = fdiv(sg, s_prob.fd_h), t = sg - r * H + 1;
       float sl;
       bound_cost(s_th[k], s_lim[j], s_lim[D + j], e2, inv_e2, sl);
       float g = s_gth[k] + prm.w_bound * sl;
