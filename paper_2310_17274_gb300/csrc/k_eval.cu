@@ -494,27 +494,37 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
           if (jl >= s_lst[l + 1] - s_lst[l]) continue;
           const int i = s_lsp[s_lst[l] + jl];
           const int k = sg * M + i;
-          const float rad = s_sph[i].w;
+          const float4 ci = s_sph[i];
+          const float rad = ci.w;
           if (rad < 0.f) continue;
           unsigned long long m0 = (unsigned long long)s_mask[2 * sl0] | ((unsigned long long)s_mask[2 * sl0 + 1] << 32);
           const int r = fdiv(sg, s_prob.fd_h);
-          // boxes within the link-level bound of this sphere's reach first
+          const int sl = slot(r, sg - r * H + 1);
+          // sphere i is on link l: its position from link l's transform
+          const V3 xp = store_x ? pos(sl, i) : tf_point(s_lt + (sl * D + l) * 12, ci.x, ci.y, ci.z);
+          const float tu = rad + s_lm[sl0];
+          // boxes within the link-level bound of this sphere's reach, two per
+          // step (independent loads; the second one repeats the first when
+          // there is none)
+          auto near_box = [&](int kk) -> bool {
+            const BoxRows& b = s_box[kk];
+            const float ux = fmaf(b.r0.x, xp.x, fmaf(b.r0.y, xp.y, fmaf(b.r0.z, xp.z, b.r0.w)));
+            const float uy = fmaf(b.r1.x, xp.x, fmaf(b.r1.y, xp.y, fmaf(b.r1.z, xp.z, b.r1.w)));
+            const float uz = fmaf(b.r2.x, xp.x, fmaf(b.r2.y, xp.y, fmaf(b.r2.z, xp.z, b.r2.w)));
+            const float mx = fmaxf(fabsf(ux) - b.h.x, 0.f);
+            const float my = fmaxf(fabsf(uy) - b.h.y, 0.f);
+            const float mz = fmaxf(fabsf(uz) - b.h.z, 0.f);
+            return fmaf(mx, mx, fmaf(my, my, mz * mz)) < tu * tu;
+          };
           unsigned long long m = 0ull;
-          {
-            const V3 xp = pos(slot(r, sg - r * H + 1), i);
-            const float tu = rad + s_lm[sg * D + s_link[i]];
-            while (m0) {
-              const int kk = __ffsll((long long)m0) - 1;
-              m0 &= m0 - 1ull;
-              const BoxRows& b = s_box[kk];
-              const float ux = fmaf(b.r0.x, xp.x, fmaf(b.r0.y, xp.y, fmaf(b.r0.z, xp.z, b.r0.w)));
-              const float uy = fmaf(b.r1.x, xp.x, fmaf(b.r1.y, xp.y, fmaf(b.r1.z, xp.z, b.r1.w)));
-              const float uz = fmaf(b.r2.x, xp.x, fmaf(b.r2.y, xp.y, fmaf(b.r2.z, xp.z, b.r2.w)));
-              const float mx = fmaxf(fabsf(ux) - b.h.x, 0.f);
-              const float my = fmaxf(fabsf(uy) - b.h.y, 0.f);
-              const float mz = fmaxf(fabsf(uz) - b.h.z, 0.f);
-              if (fmaf(mx, mx, fmaf(my, my, mz * mz)) < tu * tu) m |= 1ull << kk;
-            }
+          while (m0) {
+            const int k1 = __ffsll((long long)m0) - 1;
+            m0 &= m0 - 1ull;
+            const int k2 = m0 ? __ffsll((long long)m0) - 1 : k1;
+            m0 &= m0 - 1ull;  // no-op when m0 is 0
+            const bool n1 = near_box(k1), n2 = near_box(k2);
+            if (n1) m |= 1ull << k1;
+            if (n2) m |= 1ull << k2;
           }
           if (!m) continue;
           const int e = atomicAdd(&s_nlist, 1);
@@ -784,8 +794,9 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
       }
     }
     __syncthreads();
-    // (2b) per (state, joint): the suffix sums and the end-effector terms; the
-    //      joint-0 item also adds up the state's world cost in sphere order
+    // (2b) per (state, joint): the suffix sums and the end-effector terms;
+    //      per state, on the last threads of the CTA (idle here when S D is
+    //      below the CTA size), the state's world cost in sphere order
     for (int k = tid; k < S * D; k += nthr) {
       const int sg = fdiv(k, a.rb.fd_dof), j = k - sg * D;
       const int r = fdiv(sg, s_prob.fd_h), t = sg - r * H + 1;
@@ -806,21 +817,21 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
         acc += dot(v3(dp.x, dp.y, dp.z), cross(aj, v3(pe.x, pe.y, pe.z) - oj)) + dot(aj, v3(w.x, w.y, w.z));
       }
       s_gth[k] = acc;
-      if (j == 0) {
-        float wsum = 0.f;
-        if (K > 0) {
-          for (int w = 0; w < MW; ++w) {
-            uint32_t bits = s_nz[sg * MW + w];
-            while (bits) {
-              const int i = w * 32 + __ffs(bits) - 1;
-              bits &= bits - 1u;
-              // world cost of the sphere (beta_2 speed S, from backward pass 1)
-              if (s_sg[sg * M + i].x != 0.f) wsum += s_wc[sg * M + i];
-            }
+    }
+    for (int sg = nthr - 1 - tid; sg >= 0 && sg < S; sg += nthr) {
+      float wsum = 0.f;
+      if (K > 0) {
+        for (int w = 0; w < MW; ++w) {
+          uint32_t bits = s_nz[sg * MW + w];
+          while (bits) {
+            const int i = w * 32 + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            // world cost of the sphere (beta_2 speed S, from backward pass 1)
+            if (s_sg[sg * M + i].x != 0.f) wsum += s_wc[sg * M + i];
           }
         }
-        s_stw[sg] = wsum;
       }
+      s_stw[sg] = wsum;
     }
     __syncthreads();
 
@@ -853,8 +864,9 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
       float2* out = reinterpret_cast<float2*>(a.state_terms) + vbase / D;
       for (int k = tid; k < S; k += nthr) out[k] = make_float2(s_stw[k], selfc ? prm.w_self * s_sts[k] : 0.f);
     }
-    // ---- per-trajectory cost in a fixed order
-    for (int r = warp; r < nt; r += nw) {
+    // ---- per-trajectory cost in a fixed order, from the last warp down (the
+    // first warps still hold gradient items of this pass)
+    for (int r = nw - 1 - warp; r >= 0 && r < nt; r += nw) {
       float tw = 0.f, ts = 0.f, tb = 0.f, tsm = 0.f;
       for (int t = lane; t < H; t += 32) {
         tw += s_stw[r * H + t];
