@@ -119,7 +119,7 @@ def _rot_to_quat(R):
 EVAL_TRAFFIC = {"bytes": 604672, "states": 12288, "sources_sha256": "4b72c4df93db4376",
                 "profile": "profiles/k_eval_trajopt_32x48x8.md"}
 EVAL_SOURCES = ("paper_2310_17274_gb300/csrc/k_eval.cu", "paper_2310_17274_gb300/csrc/crgb_internal.cuh",
-                "paper_2310_17274_gb300/csrc/k_device.cuh")
+                "paper_2310_17274_gb300/csrc/k_device.cuh", "paper_2310_17274_gb300/csrc/fastdiv.h")
 
 
 def eval_traffic(states_per_launch):

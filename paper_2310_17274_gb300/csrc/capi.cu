@@ -249,7 +249,6 @@ cr_status cr_robot_create(const cr_robot_desc* d, cr_robot** out) {
   r->view.fd_sph = make_fastdiv(M);
   r->view.fd_grp = make_fastdiv(G);
   r->view.fd_lsph = make_fastdiv(max_ls);
-  r->view.fd_sphw = make_fastdiv((M + 31) / 32);
   r->view.pair_at = n_at > 0 ? reinterpret_cast<const int16_t*>(b + o_pat) : nullptr;
   r->view.link_sph4 = reinterpret_cast<const float4*>(b + o_ls4);
   for (int j = 0; j < D; ++j) {

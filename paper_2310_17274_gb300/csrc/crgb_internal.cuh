@@ -67,8 +67,8 @@ struct RobotView {
   const int16_t* pair_at;   // [M][M] grouped index of the pair {i, j} (caller's first when listed
                             //   twice) or -1; robots of up to kPairTableSpheres spheres, else nullptr
   // dividers of work-item indices (set on the host): dof, spheres, link-pair
-  // groups, largest sphere count of a link, 32-bit words of a sphere mask
-  FastDiv fd_dof, fd_sph, fd_grp, fd_lsph, fd_sphw;
+  // groups, largest sphere count of a link
+  FastDiv fd_dof, fd_sph, fd_grp, fd_lsph;
 };
 
 // One box packed as five float4 rows: (R^T row k, t_k) for k = 0..2 so that

@@ -702,20 +702,16 @@ __global__ void __launch_bounds__(512, MinBlocks) k_eval(const __grid_constant__
     //      (marked by the sweep and the self term: own sweep result, a
     //      neighbour's sweep sum through the speed, the deepest self pair);
     //      nothing reaches the others, their gradient and cost stay zero
-    for (int w = tid; w < S * MW; w += nthr) {
-      uint32_t bits = s_bwm[w];
-      if (!bits) continue;
-      const int sg = fdiv(w, a.rb.fd_sphw), i0 = (w - sg * MW) * 32;
-      int e = atomicAdd(&s_nbw, __popc(bits));
-      while (bits) {
-        const int k = sg * M + i0 + __ffs(bits) - 1;
-        bits &= bits - 1u;
-        if (e < bw_cap)
-          s_list[e] = (uint32_t)k;
-        else
-          bw1_item(k);
-        ++e;
-      }
+    // (a strided scan, so that the items past the list's capacity, run by
+    //  the thread that finds them, are spread over the CTA)
+    for (int k = tid; k < S * M; k += nthr) {
+      const int sg = fdiv(k, a.rb.fd_sph), i = k - sg * M;
+      if (!((s_bwm[sg * MW + (i >> 5)] >> (i & 31)) & 1u)) continue;
+      const int e = atomicAdd(&s_nbw, 1);
+      if (e < bw_cap)
+        s_list[e] = (uint32_t)k;
+      else
+        bw1_item(k);
     }
     __syncthreads();
     // (1b) the listed items, any thread
