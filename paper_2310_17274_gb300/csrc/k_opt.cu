@@ -109,6 +109,9 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
   __shared__ float red[2 * kRed];
   __shared__ float sh_rho[CR_MAX_HISTORY];
   __shared__ float sh_alpha[CR_MAX_HISTORY];
+  __shared__ int sh_vp[CR_MAX_HISTORY];    // slots of the pairs with rho != 0, newest first
+  __shared__ float sh_vr[CR_MAX_HISTORY];  // and their rho
+  __shared__ int sh_nv;
   int phase = 0;
 
   const int tid = threadIdx.x;
@@ -337,78 +340,111 @@ __global__ void __launch_bounds__(NT) k_opt(const __grid_constant__ OptArgs a) {
       }
       if (tid == 0) st.iter[b] = it + 1;
 
+      // the pairs with rho != 0 (inert pairs have alpha = 0 and leave q
+      // unchanged), newest first, listed once so that the recursion's slots
+      // and rows are known (and the next row loaded) ahead of each reduction
+      if (tid == 0) {
+        int nv = 0;
+        for (int i = m - 1; i >= 0; --i) {
+          int p = i + shift;
+          if (p >= m) p -= m;
+          const float rho = sh_rho[p];
+          if (rho != 0.f) {
+            sh_vp[nv] = p;
+            sh_vr[nv] = rho;
+            ++nv;
+          }
+        }
+        sh_nv = nv;
+      }
+      __syncthreads();
+      const int nv = sh_nv;
+      auto row = [&](const float* h, int p, float (&v)[SLOTS]) {
+#pragma unroll
+        for (int e = 0; e < SLOTS; ++e) {
+          const int k = tid + NT * e;
+          v[e] = k < n ? h[(long long)p * n + k] : 0.f;
+        }
+      };
       // two-loop recursion: q = g; newest to oldest
       float q[SLOTS];
 #pragma unroll
       for (int e = 0; e < SLOTS; ++e) q[e] = gr[e];
-      for (int i = m - 1; i >= 0; --i) {
-        const int p = (i + shift) % m;
-        const float rho = sh_rho[p];
-        if (rho == 0.f) {  // inert pair: alpha = 0, q unchanged
-          if (tid == 0) sh_alpha[i] = 0.f;
-          continue;
-        }
+      float sn[SLOTS];
+      if (nv > 0) row(hs, sh_vp[0], sn);
+      for (int j = 0; j < nv; ++j) {
+        const int p = sh_vp[j];
+        float sc[SLOTS], yc[SLOTS];
+#pragma unroll
+        for (int e = 0; e < SLOTS; ++e) sc[e] = sn[e];
+        row(hy, p, yc);
+        if (j + 1 < nv) row(hs, sh_vp[j + 1], sn);
         Part<NT, SLOTS> d[1];
         d[0].zero();
 #pragma unroll
         for (int e = 0; e < SLOTS; ++e) {
           const int k = tid + NT * e;
-          if (k < n) d[0].fma(e, hs[(long long)p * n + k], q[e]);
+          if (k < n) d[0].fma(e, sc[e], q[e]);
         }
         float dt[1];
         block_sum<NT, SLOTS, 1>(d, dt, red, phase);
-        const float al = rho * dt[0];
-        if (tid == 0) sh_alpha[i] = al;
+        const float al = sh_vr[j] * dt[0];
+        if (tid == 0) sh_alpha[j] = al;
 #pragma unroll
         for (int e = 0; e < SLOTS; ++e) {
           const int k = tid + NT * e;
-          if (k < n) q[e] = fmaf(-al, hy[(long long)p * n + k], q[e]);
+          if (k < n) q[e] = fmaf(-al, yc[e], q[e]);
         }
       }
-      // H0 = gamma I from the newest valid pair
+      // H0 = gamma I from the newest valid pair (rho = 1 / y.s when
+      // y.s > 1e-8, else 0: never negative or NaN, so the first listed pair)
       float gamma = 1.f;
-      for (int i = m - 1; i >= 0; --i) {
-        const int p = (i + shift) % m;
-        if (sh_rho[p] > 0.f) {
-          Part<NT, SLOTS> d[2];
-          d[0].zero();
-          d[1].zero();
+      if (nv > 0) {
+        float sv[SLOTS], yv[SLOTS];
+        row(hs, sh_vp[0], sv);
+        row(hy, sh_vp[0], yv);
+        Part<NT, SLOTS> d[2];
+        d[0].zero();
+        d[1].zero();
 #pragma unroll
-          for (int e = 0; e < SLOTS; ++e) {
-            const int k = tid + NT * e;
-            if (k < n) {
-              const float sv = hs[(long long)p * n + k], yv = hy[(long long)p * n + k];
-              d[0].fma(e, sv, yv);
-              d[1].fma(e, yv, yv);
-            }
+        for (int e = 0; e < SLOTS; ++e) {
+          const int k = tid + NT * e;
+          if (k < n) {
+            d[0].fma(e, sv[e], yv[e]);
+            d[1].fma(e, yv[e], yv[e]);
           }
-          float dt[2];
-          block_sum<NT, SLOTS, 2>(d, dt, red, phase);
-          gamma = dt[0] / dt[1];
-          break;
         }
+        float dt[2];
+        block_sum<NT, SLOTS, 2>(d, dt, red, phase);
+        gamma = dt[0] / dt[1];
       }
 #pragma unroll
       for (int e = 0; e < SLOTS; ++e) q[e] *= gamma;
       __syncthreads();  // sh_alpha visible
-      for (int i = 0; i < m; ++i) {
-        const int p = (i + shift) % m;
-        const float rho = sh_rho[p];
-        if (rho == 0.f) continue;
+      // oldest to newest
+      float yn[SLOTS];
+      if (nv > 0) row(hy, sh_vp[nv - 1], yn);
+      for (int j = nv - 1; j >= 0; --j) {
+        const int p = sh_vp[j];
+        float yc[SLOTS], sc[SLOTS];
+#pragma unroll
+        for (int e = 0; e < SLOTS; ++e) yc[e] = yn[e];
+        row(hs, p, sc);
+        if (j > 0) row(hy, sh_vp[j - 1], yn);
         Part<NT, SLOTS> d[1];
         d[0].zero();
 #pragma unroll
         for (int e = 0; e < SLOTS; ++e) {
           const int k = tid + NT * e;
-          if (k < n) d[0].fma(e, hy[(long long)p * n + k], q[e]);
+          if (k < n) d[0].fma(e, yc[e], q[e]);
         }
         float dt[1];
         block_sum<NT, SLOTS, 1>(d, dt, red, phase);
-        const float coef = sh_alpha[i] - rho * dt[0];
+        const float coef = sh_alpha[j] - sh_vr[j] * dt[0];
 #pragma unroll
         for (int e = 0; e < SLOTS; ++e) {
           const int k = tid + NT * e;
-          if (k < n) q[e] = fmaf(hs[(long long)p * n + k], coef, q[e]);
+          if (k < n) q[e] = fmaf(sc[e], coef, q[e]);
         }
       }
       // direction and the clipped candidates of Alg. 1
