@@ -458,7 +458,10 @@ void cr_server_destroy(cr_server* server);
  * requests already wait. */
 cr_status cr_server_submit(cr_server* server, int32_t kind, const cr_problem* problem,
                            uint64_t* ticket);
-/* One step; never waits for the device.  For every pool: if its last round
+/* One step.  It does not wait for the device, except while a pool grows or
+ * a table buffer is enlarged: the live slots are copied into the new arrays
+ * and the old ones freed, and freeing device memory can wait for the device
+ * (a pool at its working size never does this).  For every pool: if its last round
  * has finished, the requests that retired in it become done (results already
  * in pinned host memory) and their slots free; queued requests are admitted
  * into free slots of idle pools (first come, first served per pool), a pool

@@ -9,7 +9,9 @@
 // with room for `capacity` slots, slot s owning seeds s*B .. s*B + B - 1.
 // Each pool has its own stream and runs independently of the others.
 //
-// cr_server_step never waits for the device.  For every pool it
+// cr_server_step does not wait for the device, except while a pool grows or
+// its table buffer is enlarged (the live slots are copied over and the old
+// arrays freed, which can wait for the device).  For every pool it
 //   1. collects the pool's last round if the round has finished (results of
 //      the requests that retired in it, already copied to pinned host
 //      memory; their slots become free);
